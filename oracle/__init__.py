@@ -1,0 +1,149 @@
+"""FP64 CPU oracle for multigrid hierarchical decomposition / recomposition.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library
+(``paper_2105_12764_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in ``mgr_oracle.c`` (plain C, FP64, the steps of
+Section II.A of arXiv 2105.12764 in the paper's order); this module is a
+ctypes wrapper around it.  Every function here is pinned by the
+``-m "not gpu"`` tests in ``tests/test_oracle_pins.py``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_max_levels.argtypes = [ctypes.c_int, i64p]
+        lib.oracle_max_levels.restype = ctypes.c_int
+        lib.oracle_default_levels.argtypes = [ctypes.c_int, i64p]
+        lib.oracle_default_levels.restype = ctypes.c_int
+        for name in ("oracle_decompose", "oracle_recompose"):
+            f = getattr(lib, name)
+            f.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(dp), ctypes.c_int, dp, dp]
+            f.restype = ctypes.c_int
+        lib.oracle_mass_1d.argtypes = [ctypes.c_int64, dp, dp, dp, dp]
+        lib.oracle_mass_1d.restype = None
+        lib.oracle_transfer_1d.argtypes = [ctypes.c_int64, dp, dp]
+        lib.oracle_transfer_1d.restype = ctypes.c_int64
+        lib.oracle_interp_1d.argtypes = [ctypes.c_int64, dp, dp]
+        lib.oracle_interp_1d.restype = ctypes.c_int64
+        _lib = lib
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _shape_arr(shape):
+    return (ctypes.c_int64 * len(shape))(*[int(s) for s in shape])
+
+
+def max_levels(shape):
+    """Deepest allowed hierarchy: coarsenings until the smallest dimension has 2 nodes."""
+    lib = _load()
+    r = lib.oracle_max_levels(len(shape), _shape_arr(shape))
+    if r < 0:
+        raise ValueError(f"invalid shape {shape}")
+    return r
+
+
+def default_levels(shape):
+    """Default depth (levels=-1): coarsenings until the smallest dimension has 3 nodes."""
+    lib = _load()
+    r = lib.oracle_default_levels(len(shape), _shape_arr(shape))
+    if r < 0:
+        raise ValueError(f"invalid shape {shape}")
+    return r
+
+
+def _coords_arg(shape, coords):
+    keep = []
+    arr = (ctypes.POINTER(ctypes.c_double) * len(shape))()
+    for k in range(len(shape)):
+        c = None if coords is None else coords[k]
+        if c is None:
+            arr[k] = ctypes.POINTER(ctypes.c_double)()
+        else:
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            if c.shape != (shape[k],):
+                raise ValueError("coordinate array length must match the shape")
+            keep.append(c)
+            arr[k] = _dptr(c)
+    return arr, keep
+
+
+def _run(fn, u, coords, levels):
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty_like(u)
+    carr, keep = _coords_arg(u.shape, coords)
+    rc = getattr(lib, fn)(u.ndim, _shape_arr(u.shape), carr, int(levels), _dptr(u), _dptr(out))
+    del keep
+    if rc == -1:
+        raise ValueError(f"{fn}: invalid arguments (shape {u.shape}, levels {levels})")
+    if rc != 0:
+        raise MemoryError(f"{fn}: allocation failed ({rc})")
+    return out
+
+
+def decompose(u, coords=None, levels=-1):
+    """Nodal-layout hierarchical coefficients of ``u`` (FP64), Section II.A."""
+    return _run("oracle_decompose", u, coords, levels)
+
+
+def recompose(c, coords=None, levels=-1):
+    """Inverse of :func:`decompose` (Section II.A, recomposition)."""
+    return _run("oracle_recompose", c, coords, levels)
+
+
+def mass_1d(x):
+    """(sub, diag, super) of the P1 mass matrix on coordinates ``x``."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    a, b, c = np.empty(n), np.empty(n), np.empty(n)
+    lib.oracle_mass_1d(n, _dptr(x), _dptr(a), _dptr(b), _dptr(c))
+    return a, b, c
+
+
+def transfer_1d(x):
+    """Dense K = P^T M (m x n) of one level with fine coordinates ``x``."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    m = lib.oracle_transfer_1d(n, _dptr(x), ctypes.POINTER(ctypes.c_double)())
+    K = np.empty((m, n))
+    lib.oracle_transfer_1d(n, _dptr(x), _dptr(K))
+    return K
+
+
+def interp_1d(x):
+    """Dense interpolation P (n x m) of one level with fine coordinates ``x``."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    m = lib.oracle_interp_1d(n, _dptr(x), ctypes.POINTER(ctypes.c_double)())
+    P = np.empty((n, m))
+    lib.oracle_interp_1d(n, _dptr(x), _dptr(P))
+    return P
+
+
+def library_path():
+    return _build.build()
+
+
+__all__ = ["max_levels", "default_levels", "decompose", "recompose", "mass_1d", "transfer_1d", "interp_1d"]
