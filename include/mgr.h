@@ -1,0 +1,147 @@
+/*
+ * mgr.h -- C ABI of the GB300 (sm_103a) multigrid hierarchical data
+ * refactoring library: decomposition of a structured-grid field into
+ * hierarchical coefficients and its inverse recomposition
+ * (arXiv 2105.12764, Sec. II.A, Eq. (1) and Eq. (2)).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns int: MGR_OK (0) on success, a negative MGR_E*
+ *     code otherwise; mgr_strerror() names it.  No C++ exception crosses the
+ *     ABI.  A failing call leaves caller-owned buffers untouched unless it
+ *     says otherwise.
+ *   - Pointers named `in`, `out`, `workspace` are DEVICE pointers on the
+ *     context's device (cudaMalloc, torch, ...), owned by the caller.  Pointers
+ *     in mgr_desc.coords are HOST pointers, copied at plan creation.
+ *   - Arrays are row-major: shape[ndim-1] is the fastest (contiguous) axis.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it and the call returns without waiting, unless stated.
+ *
+ * Output layout ("nodal"): decomposition output has the input's shape.  The
+ * node sets of the hierarchy are nested, N_0 c N_1 c ... c N_L (all nodes);
+ * every node of N_l \ N_{l-1} holds its level-l coefficient
+ * (I - Pi_{l-1}) Q_l u (Sec. II.A.1), and the nodes of N_0 hold the coarsest
+ * nodal values Q_0 u.  Per dimension, the level-(l-1) node list keeps every
+ * other node of the level-l list starting with the first one, plus the last
+ * node if it was skipped; for n = 2^k+1 this is the paper's dyadic hierarchy.
+ */
+#ifndef MGR_H
+#define MGR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define MGR_OK 0
+#define MGR_EINVAL (-1)    /* invalid argument (shape, levels, alias, NULL, ...)   */
+#define MGR_ENOMEM (-2)    /* host or device allocation failed                     */
+#define MGR_EBUDGET (-3)   /* request can never fit the context's memory budget    */
+#define MGR_ECUDA (-4)     /* a CUDA runtime call failed (sticky errors included)  */
+#define MGR_EPENDING (-5)  /* poll: work not finished yet                          */
+#define MGR_ETIMEDOUT (-6) /* poll/wait: the timeout expired                       */
+#define MGR_EDEVICE (-7)   /* a kernel reported an error through the device word   */
+#define MGR_ENOTFOUND (-8) /* unknown ticket / resident handle                     */
+#define MGR_EBUSY (-9)     /* queue full: retry after polling                      */
+
+typedef struct CUstream_st* mgr_stream_t; /* same type as cudaStream_t */
+
+typedef enum { MGR_F32 = 0, MGR_F64 = 1 } mgr_dtype;
+
+typedef enum {
+  /* every step in the field's dtype */
+  MGR_PREC_NATIVE = 0,
+  /* the precision pattern: coefficients and mass-transfer stencils in FP32,
+     tridiagonal solves, correction accumulation and the coarse-grid
+     workspace in FP64.  Requires dtype MGR_F32. */
+  MGR_PREC_MIXED = 1
+} mgr_precision;
+
+/* Problem description (Sec. II.A: a d-dimensional field on a rectilinear
+   grid; Sec. IV.A: FP32 or FP64 nodal values). */
+typedef struct {
+  int ndim;                /* 1..3                                                   */
+  int64_t shape[4];        /* shape[0..ndim-1], each >= 2; shape[ndim-1] fastest     */
+  const double* coords[4]; /* HOST, strictly increasing, length shape[k]; NULL means
+                              uniform unit spacing x_i = i.  Copied at plan time;
+                              spacings are formed in FP64 on the host.               */
+  int levels;              /* -1: default depth (smallest dimension reaches 3 nodes);
+                              0..mgr_max_levels(): explicit depth                    */
+  mgr_dtype dtype;
+  mgr_precision prec;
+} mgr_desc;
+
+typedef struct mgr_ctx mgr_ctx;
+typedef struct mgr_plan mgr_plan;
+
+const char* mgr_strerror(int code);
+
+/* Library version, "major.minor.patch". */
+const char* mgr_version(void);
+
+/* Create a context on CUDA device `device` (made current on this thread).
+   mem_budget_bytes caps the device memory the context's batch / serving
+   layer may hold (0 = no cap).  Owns the streams, graphs, autotune cache and
+   resident pool.  *ctx is NULL on failure. */
+int mgr_init(int device, size_t mem_budget_bytes, mgr_ctx** ctx);
+/* Synchronises the context's streams and frees everything it owns.  Plans
+   created from it must be destroyed first. */
+int mgr_shutdown(mgr_ctx* ctx);
+
+/* Deepest explicit depth (smallest dimension reaches 2 nodes) and the default
+   depth (smallest dimension reaches 3 nodes) for a description. */
+int mgr_max_levels(const mgr_desc* desc, int* levels);
+int mgr_default_levels(const mgr_desc* desc, int* levels);
+
+/* Build a plan: the hierarchy, every interpolation weight, the mass-transfer
+   stencils K = P^T M (Sec. III.A.2, formed as P^T M in FP64 from the
+   coordinates) and the factors of the coarse mass matrices for the Thomas
+   solves (Sec. III.A.3), uploaded once to the device.  The plan owns these
+   device arrays; it holds no field data. */
+int mgr_plan_create(mgr_ctx* ctx, const mgr_desc* desc, mgr_plan** plan);
+int mgr_plan_destroy(mgr_plan* plan);
+/* Depth the plan runs (levels = -1 resolved). */
+int mgr_plan_levels(const mgr_plan* plan, int* levels);
+/* Bytes of device workspace one mgr_decompose / mgr_recompose call needs
+   (coarse-grid buffers: about 0.27 x the field's element count, in the
+   solve precision).  May be 0 when levels = 0. */
+int mgr_workspace_size(const mgr_plan* plan, size_t* bytes);
+
+/* Decompose (Sec. II.A, finest to coarsest): for l = L..1 compute the level-l
+   coefficients (interpolation residuals), the load vector f = (x_k P_k^T M_k) c,
+   the correction z from the tensor-product coarse mass matrix by Thomas
+   solves along every dimension, and add z to the coarse nodes.
+     in        DEVICE, prod(shape) elements of dtype, row-major
+     out       DEVICE, same size and type, nodal layout (above); out == in
+               (exact alias) is allowed, partial overlap returns MGR_EINVAL
+     workspace DEVICE, >= mgr_workspace_size() bytes, 256-byte aligned; its
+               contents on entry do not matter
+   Asynchronous on `stream`; the buffers must stay valid until the stream
+   reaches this point.  Concurrent calls that share a workspace race. */
+int mgr_decompose(const mgr_plan* plan, const void* in, void* out, void* workspace, mgr_stream_t stream);
+
+/* Recompose (Sec. II.A, coarsest to finest): the inverse of mgr_decompose.
+   For l = 1..L recompute z from the level-l coefficients, subtract it from
+   the coarse nodes, and add the interpolant of the coarse nodes to the
+   coefficients.  Arguments as for mgr_decompose (in = nodal coefficients,
+   out = field). */
+int mgr_recompose(const mgr_plan* plan, const void* in, void* out, void* workspace, mgr_stream_t stream);
+
+/* End-to-end forms for callers that hold the field in HOST memory: copy
+   host_in to dev_in, run the operation from dev_in into dev_out, and copy
+   dev_out back to host_out, all on `stream` (pinned host memory makes the
+   copies asynchronous).  dev_in, dev_out: DEVICE, field-sized; they may be
+   the same buffer.  Returns after enqueueing; synchronise `stream` before
+   reading host_out. */
+int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
+                       void* workspace, mgr_stream_t stream);
+int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
+                       void* workspace, mgr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGR_H */

@@ -1,0 +1,213 @@
+"""Python binding of the GB300 multigrid hierarchical refactoring library.
+
+Argument marshalling only: every step of decomposition / recomposition runs
+in the CUDA kernels of ``libmgr.so`` (built from ``csrc/`` for sm_103a).
+The functions carry the names of the C ABI in ``include/mgr.h``; the small
+``Context`` / ``Plan`` classes only hold handles and pass device pointers
+(``torch.Tensor.data_ptr()``) and CUDA stream handles through.
+
+There is no CPU fallback: importing this package raises if ``libmgr.so`` is
+missing (build it with ``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+import ctypes
+import os
+
+__all__ = [
+    "MGR_OK", "MGR_EINVAL", "MGR_ENOMEM", "MGR_EBUDGET", "MGR_ECUDA", "MGR_EPENDING", "MGR_ETIMEDOUT",
+    "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
+    "MgrError", "mgr_desc", "lib", "library_path", "Context", "Plan", "EXPORTED",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libmgr.so")
+
+MGR_OK, MGR_EINVAL, MGR_ENOMEM, MGR_EBUDGET, MGR_ECUDA = 0, -1, -2, -3, -4
+MGR_EPENDING, MGR_ETIMEDOUT, MGR_EDEVICE, MGR_ENOTFOUND, MGR_EBUSY = -5, -6, -7, -8, -9
+MGR_F32, MGR_F64 = 0, 1
+MGR_PREC_NATIVE, MGR_PREC_MIXED = 0, 1
+
+
+class MgrError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__(f"{fn} failed: {mgr_strerror(code)} ({code})")
+
+
+class mgr_desc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("shape", ctypes.c_int64 * 4),
+        ("coords", ctypes.POINTER(ctypes.c_double) * 4),
+        ("levels", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("prec", ctypes.c_int),
+    ]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+# name -> (restype, argtypes): every entry point declared in include/mgr.h
+EXPORTED = {
+    "mgr_strerror": (ctypes.c_char_p, [_i]),
+    "mgr_version": (ctypes.c_char_p, []),
+    "mgr_init": (_i, [_i, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "mgr_shutdown": (_i, [_vp]),
+    "mgr_max_levels": (_i, [ctypes.POINTER(mgr_desc), ctypes.POINTER(_i)]),
+    "mgr_default_levels": (_i, [ctypes.POINTER(mgr_desc), ctypes.POINTER(_i)]),
+    "mgr_plan_create": (_i, [_vp, ctypes.POINTER(mgr_desc), ctypes.POINTER(_vp)]),
+    "mgr_plan_destroy": (_i, [_vp]),
+    "mgr_plan_levels": (_i, [_vp, ctypes.POINTER(_i)]),
+    "mgr_workspace_size": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "mgr_decompose": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mgr_recompose": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mgr_decompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+}
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"{_LIB_PATH} is missing: the multigrid library has no CPU fallback; build it with "
+            "`python -c \"import __graft_entry__ as g; g.build()\"`")
+    handle = ctypes.CDLL(_LIB_PATH)
+    for name, (res, args) in EXPORTED.items():
+        f = getattr(handle, name)
+        f.restype = res
+        f.argtypes = args
+    return handle
+
+
+lib = _load()
+
+
+def mgr_strerror(code):
+    return lib.mgr_strerror(int(code)).decode()
+
+
+def _check(fn, rc):
+    if rc != MGR_OK:
+        raise MgrError(fn, rc)
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def make_desc(shape, coords=None, levels=-1, dtype=MGR_F64, prec=MGR_PREC_NATIVE):
+    """Fill an mgr_desc; returns (desc, keepalive) -- keep both alive until plan creation returns."""
+    import numpy as np
+
+    d = mgr_desc()
+    d.ndim = len(shape)
+    for k, s in enumerate(shape):
+        d.shape[k] = int(s)
+    keep = []
+    for k in range(len(shape)):
+        c = None if coords is None else coords[k]
+        if c is not None:
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            keep.append(c)
+            d.coords[k] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.levels = int(levels)
+    d.dtype = int(dtype)
+    d.prec = int(prec)
+    return d, keep
+
+
+class Context:
+    """mgr_init / mgr_shutdown."""
+
+    def __init__(self, device=0, mem_budget_bytes=0):
+        h = _vp()
+        _check("mgr_init", lib.mgr_init(int(device), int(mem_budget_bytes), ctypes.byref(h)))
+        self.handle = h.value
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _check("mgr_shutdown", lib.mgr_shutdown(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Plan:
+    """mgr_plan_create / mgr_decompose / mgr_recompose on device pointers."""
+
+    def __init__(self, ctx, shape, coords=None, levels=-1, dtype=MGR_F64, prec=MGR_PREC_NATIVE):
+        d, keep = make_desc(shape, coords, levels, dtype, prec)
+        h = _vp()
+        _check("mgr_plan_create", lib.mgr_plan_create(ctx.handle, ctypes.byref(d), ctypes.byref(h)))
+        del keep
+        self.handle = h.value
+        self.ctx = ctx
+        self.shape = tuple(int(s) for s in shape)
+        self.dtype = dtype
+        self.prec = prec
+        lv = _i()
+        _check("mgr_plan_levels", lib.mgr_plan_levels(self.handle, ctypes.byref(lv)))
+        self.levels = lv.value
+        ws = ctypes.c_size_t()
+        _check("mgr_workspace_size", lib.mgr_workspace_size(self.handle, ctypes.byref(ws)))
+        self.workspace_bytes = ws.value
+
+    def decompose(self, inp, out, workspace, stream=None):
+        _check("mgr_decompose", lib.mgr_decompose(self.handle, _ptr(inp), _ptr(out), _ptr(workspace), _stream(stream)))
+
+    def recompose(self, inp, out, workspace, stream=None):
+        _check("mgr_recompose", lib.mgr_recompose(self.handle, _ptr(inp), _ptr(out), _ptr(workspace), _stream(stream)))
+
+    def decompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
+        _check("mgr_decompose_host", lib.mgr_decompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),
+                                                            _ptr(dev_out), _ptr(workspace), _stream(stream)))
+
+    def recompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
+        _check("mgr_recompose_host", lib.mgr_recompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),
+                                                            _ptr(dev_out), _ptr(workspace), _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _check("mgr_plan_destroy", lib.mgr_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def max_levels(shape):
+    d, keep = make_desc(shape)
+    v = _i()
+    _check("mgr_max_levels", lib.mgr_max_levels(ctypes.byref(d), ctypes.byref(v)))
+    return v.value
+
+
+def default_levels(shape):
+    d, keep = make_desc(shape)
+    v = _i()
+    _check("mgr_default_levels", lib.mgr_default_levels(ctypes.byref(d), ctypes.byref(v)))
+    return v.value

@@ -1,0 +1,281 @@
+// mgr_api.cpp -- C ABI entry points (include/mgr.h): context, plans,
+// workspace sizing, argument checks, and the CUDA-graph cache that replays a
+// plan's whole launch sequence (all levels) as one graph launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "mgr_internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+int check_sticky() {
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ECUDA;
+  }
+  return MGR_OK;
+}
+
+int check_op_args(const mgr_plan* p, const void* in, const void* out, const void* ws) {
+  if (!p || !in || !out) return MGR_EINVAL;
+  const size_t bytes = size_t(p->count) * p->elem;
+  if ((reinterpret_cast<uintptr_t>(in) % p->elem) || (reinterpret_cast<uintptr_t>(out) % p->elem)) return MGR_EINVAL;
+  if (in != out && ranges_overlap(in, bytes, out, bytes)) return MGR_EINVAL;
+  if (p->ws_bytes > 0) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign)) return MGR_EINVAL;
+    if (ranges_overlap(ws, p->ws_bytes, in, bytes) || ranges_overlap(ws, p->ws_bytes, out, bytes)) return MGR_EINVAL;
+  }
+  return MGR_OK;
+}
+
+enum { OP_DEC = 0, OP_REC = 1 };
+
+cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st) {
+  return op == OP_DEC ? mgr::enqueue_decompose(p, in, out, ws, st) : mgr::enqueue_recompose(p, in, out, ws, st);
+}
+
+// Launch through a cached CUDA graph of the plan's launch sequence.  When the
+// caller's stream is itself being captured the kernels are enqueued directly
+// (they become part of the caller's graph).
+int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cudaStream_t st) {
+  mgr_plan* p = const_cast<mgr_plan*>(cp);
+  int rc = check_op_args(p, in, out, ws);
+  if (rc != MGR_OK) return rc;
+  if ((rc = check_sticky()) != MGR_OK) return rc;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return enqueue(p, op, in, out, ws, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+
+  std::lock_guard<std::mutex> lk(p->graph_mu);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : p->graphs)
+    if (g.op == op && g.in == in && g.out == out && g.ws == ws) exec = g.exec;
+  if (!exec) {
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MGR_ECUDA;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue(p, op, in, out, ws, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return MGR_ECUDA;
+    }
+    if (p->graphs.size() >= 8) {
+      cudaGraphExecDestroy(p->graphs.front().exec);
+      p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back({op, in, out, ws, exec});
+  }
+  return cudaGraphLaunch(exec, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+}
+
+int run_host(const mgr_plan* p, int op, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
+             cudaStream_t st) {
+  if (!p || !host_in || !host_out || !dev_in || !dev_out) return MGR_EINVAL;
+  const size_t bytes = size_t(p->count) * p->elem;
+  if (cudaMemcpyAsync(dev_in, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return MGR_ECUDA;
+  int rc = run_op(p, op, dev_in, dev_out, ws, st);
+  if (rc != MGR_OK) return rc;
+  if (cudaMemcpyAsync(host_out, dev_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MGR_ECUDA;
+  return MGR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mgr_strerror(int code) {
+  switch (code) {
+    case MGR_OK: return "ok";
+    case MGR_EINVAL: return "invalid argument";
+    case MGR_ENOMEM: return "out of memory";
+    case MGR_EBUDGET: return "request exceeds the memory budget";
+    case MGR_ECUDA: return "CUDA error";
+    case MGR_EPENDING: return "pending";
+    case MGR_ETIMEDOUT: return "timed out";
+    case MGR_EDEVICE: return "device-side error reported";
+    case MGR_ENOTFOUND: return "not found";
+    case MGR_EBUSY: return "queue full";
+    default: return "unknown error";
+  }
+}
+
+const char* mgr_version(void) { return "0.1.0"; }
+
+int mgr_init(int device, size_t mem_budget_bytes, mgr_ctx** ctx) {
+  if (!ctx) return MGR_EINVAL;
+  *ctx = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ECUDA;
+  }
+  if (device < 0 || device >= n) return MGR_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return MGR_ECUDA;
+  mgr_ctx* c = new (std::nothrow) mgr_ctx();
+  if (!c) return MGR_ENOMEM;
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  c->num_sms = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = size_t(v);
+  *ctx = c;
+  return MGR_OK;
+}
+
+int mgr_shutdown(mgr_ctx* ctx) {
+  if (!ctx) return MGR_EINVAL;
+  if (ctx->live_plans.load() != 0) return MGR_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+  return MGR_OK;
+}
+
+int mgr_max_levels(const mgr_desc* desc, int* levels) {
+  if (!levels) return MGR_EINVAL;
+  return mgr::resolve_levels(desc, nullptr, levels, nullptr);
+}
+
+int mgr_default_levels(const mgr_desc* desc, int* levels) {
+  if (!levels) return MGR_EINVAL;
+  return mgr::resolve_levels(desc, nullptr, nullptr, levels);
+}
+
+int mgr_plan_create(mgr_ctx* ctx, const mgr_desc* desc, mgr_plan** plan) {
+  if (!ctx || !desc || !plan) return MGR_EINVAL;
+  *plan = nullptr;
+  if (desc->dtype != MGR_F32 && desc->dtype != MGR_F64) return MGR_EINVAL;
+  if (desc->prec != MGR_PREC_NATIVE && desc->prec != MGR_PREC_MIXED) return MGR_EINVAL;
+  if (desc->prec == MGR_PREC_MIXED && desc->dtype != MGR_F32) return MGR_EINVAL;
+  int L = 0;
+  int rc = mgr::resolve_levels(desc, &L, nullptr, nullptr);
+  if (rc != MGR_OK) return rc;
+  mgr_plan* p = new (std::nothrow) mgr_plan();
+  if (!p) return MGR_ENOMEM;
+  p->ctx = ctx;
+  p->desc = *desc;
+  for (int k = desc->ndim; k < 4; ++k) {
+    p->desc.shape[k] = 0;
+    p->desc.coords[k] = nullptr;
+  }
+  p->levels = L;
+  p->form = desc->dtype == MGR_F64 ? mgr::kFormF64 : (desc->prec == MGR_PREC_MIXED ? mgr::kFormMixed : mgr::kFormF32);
+  p->elem = desc->dtype == MGR_F64 ? 8 : 4;
+  p->welem = (p->form == mgr::kFormF32) ? 4 : 8;
+  p->count = 1;
+  for (int k = 0; k < desc->ndim; ++k) p->count *= desc->shape[k];
+  try {
+    rc = mgr::build_plan_tables(p);
+  } catch (const std::bad_alloc&) {
+    rc = MGR_ENOMEM;
+  }
+  // the coordinate pointers are not kept: the tables hold everything needed
+  for (int k = 0; k < 4; ++k) p->desc.coords[k] = nullptr;
+  if (rc != MGR_OK) {
+    delete p;
+    return rc;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    delete p;
+    return MGR_ECUDA;
+  }
+  const size_t nt = std::max<size_t>(p->tables.host.size(), 4);
+  std::vector<float> f32(nt, 0.0f);
+  for (size_t i = 0; i < p->tables.host.size(); ++i) f32[i] = float(p->tables.host[i]);
+  std::vector<double> f64(nt, 0.0);
+  std::copy(p->tables.host.begin(), p->tables.host.end(), f64.begin());
+  if (cudaMalloc(&p->tables.d64, nt * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&p->tables.d32, nt * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p->tables.d64);
+    cudaFree(p->tables.d32);
+    delete p;
+    return MGR_ENOMEM;
+  }
+  if (cudaMemcpy(p->tables.d64, f64.data(), nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->tables.d32, f32.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(p->tables.d64);
+    cudaFree(p->tables.d32);
+    delete p;
+    return MGR_ECUDA;
+  }
+  if (L >= 1) {
+    p->ws_a = align_up(size_t(p->geom[L].coarse_count()) * p->welem);
+    p->ws_b = L >= 2 ? align_up(size_t(p->geom[L - 1].coarse_count()) * p->welem) : 0;
+    p->ws_f = align_up(size_t(p->geom[L].coarse_count()) * p->welem);
+  }
+  p->ws_bytes = p->ws_a + p->ws_b + p->ws_f;
+  ctx->live_plans.fetch_add(1);
+  *plan = p;
+  return MGR_OK;
+}
+
+int mgr_plan_destroy(mgr_plan* p) {
+  if (!p) return MGR_EINVAL;
+  cudaSetDevice(p->ctx->device);
+  {
+    std::lock_guard<std::mutex> lk(p->graph_mu);
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+  }
+  cudaFree(p->tables.d64);
+  cudaFree(p->tables.d32);
+  p->ctx->live_plans.fetch_sub(1);
+  delete p;
+  return MGR_OK;
+}
+
+int mgr_plan_levels(const mgr_plan* p, int* levels) {
+  if (!p || !levels) return MGR_EINVAL;
+  *levels = p->levels;
+  return MGR_OK;
+}
+
+int mgr_workspace_size(const mgr_plan* p, size_t* bytes) {
+  if (!p || !bytes) return MGR_EINVAL;
+  *bytes = p->ws_bytes;
+  return MGR_OK;
+}
+
+int mgr_decompose(const mgr_plan* p, const void* in, void* out, void* ws, mgr_stream_t stream) {
+  return run_op(p, OP_DEC, in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgr_recompose(const mgr_plan* p, const void* in, void* out, void* ws, mgr_stream_t stream) {
+  return run_op(p, OP_REC, in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgr_decompose_host(const mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
+                       mgr_stream_t stream) {
+  return run_host(p, OP_DEC, host_in, host_out, dev_in, dev_out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgr_recompose_host(const mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
+                       mgr_stream_t stream) {
+  return run_host(p, OP_REC, host_in, host_out, dev_in, dev_out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

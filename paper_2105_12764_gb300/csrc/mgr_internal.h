@@ -1,0 +1,106 @@
+// mgr_internal.h -- internal types of the GB300 multigrid refactoring library.
+//
+// Axes are always handled as three: axis 0 (slowest) .. axis 2 (fastest).  A
+// field with ndim < 3 is embedded with leading axes of length 1 that never
+// coarsen ("inactive").
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "mgr.h"
+
+namespace mgr {
+
+constexpr int kAxes = 3;
+constexpr int kMaxLevels = 60;
+
+// Element type combination of one plan ("form").
+enum Form : int {
+  kFormF64 = 0,    // FP64 field, every step in FP64
+  kFormF32 = 1,    // FP32 field, every step in FP32
+  kFormMixed = 2,  // FP32 field, FP32 stencils, FP64 solves/accumulation/coarse workspace
+};
+
+// One axis at one level.  Level-l node i of this axis sits at full-grid index
+// min(i * s, N - 1) (the keep-last nesting of the hierarchy).
+struct AxisLevel {
+  int n = 1;            // nodes on this axis at level l
+  int m = 1;            // nodes at level l-1
+  int64_t s = 1;        // full-grid stride 2^(L-l)
+  int64_t N = 1;        // full-grid length of the axis
+  bool active = false;  // coarsens at this level (n >= 3)
+  // element offsets into the plan's weight tables
+  int64_t o_wa = 0, o_wb = 0;  // interpolation weights, indexed by fine node (n entries)
+  int64_t o_k = 0;             // 5 * m mass-transfer taps, row q at offsets -2..2 around node min(2q, n-1),
+                               // each row scaled by 1/u_q of the coarse mass matrix's LU factors
+  int64_t o_ta = 0, o_tb = 0;  // scaled Thomas recurrences, m entries each
+};
+
+struct LevelGeom {
+  AxisLevel ax[kAxes];
+  int64_t fine_count() const { return (int64_t)ax[0].n * ax[1].n * ax[2].n; }
+  int64_t coarse_count() const { return (int64_t)ax[0].m * ax[1].m * ax[2].m; }
+};
+
+// Host-side FP64 tables of a plan (built from the coordinates) and their
+// device copies in FP64 and FP32.
+struct Tables {
+  std::vector<double> host;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+};
+
+}  // namespace mgr
+
+struct mgr_ctx {
+  int device = 0;
+  size_t budget = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  std::atomic<int> live_plans{0};
+  void* batch = nullptr;  // batch / serving state (mgr_batch.cu)
+};
+
+struct mgr_plan {
+  mgr_ctx* ctx = nullptr;
+  mgr_desc desc{};
+  int form = 0;
+  int levels = 0;                     // L
+  int64_t full[mgr::kAxes] = {1, 1, 1};
+  int64_t count = 0;                  // prod(shape)
+  size_t elem = 0;                    // bytes per field element
+  size_t welem = 0;                   // bytes per workspace element
+  std::vector<mgr::LevelGeom> geom;   // geom[l] for l = 1..L (geom[0] unused)
+  int64_t coarsest[mgr::kAxes] = {1, 1, 1};
+  mgr::Tables tables;
+  // workspace layout (bytes)
+  size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_bytes = 0;
+  // launch-sequence cache: one CUDA graph per (op, in, out, workspace)
+  std::mutex graph_mu;
+  struct GraphEntry {
+    int op;
+    const void* in;
+    void* out;
+    void* ws;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+};
+
+namespace mgr {
+
+// mgr_plan.cpp
+int build_plan_tables(mgr_plan* p);
+int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels);
+
+// mgr_core.cu: enqueue one whole operation (all levels) on `st` (no graph).
+cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+
+}  // namespace mgr

@@ -1,0 +1,193 @@
+// mgr_plan.cpp -- host-side plan construction (FP64).
+//
+// For every level l = L..1 and every axis this builds, from the axis
+// coordinates (arXiv 2105.12764, Sec. III.A.2 "r_i = h_i/(h_i+h_{i+1})"):
+//   * the interpolation weights of the fine nodes (Sec. II.A.1, Fig.
+//     example-1d; the FMA form of Table "fma" uses the right-neighbour weight
+//     r, we keep both weights so no 1-r cancellation happens on stretched grids);
+//   * the mass-transfer stencil K = P^T M (Sec. III.A.2; the paper prints K
+//     with a garbled diagonal entry, so K is formed here as the product P^T M
+//     of the interpolation and the P1 mass matrix, five taps per coarse node);
+//   * the LU factors of the coarse mass matrix M_{l-1} for the Thomas solves
+//     (Sec. III.A.3; Table "fma" rows "Solv. Corr.": precomputed diag/subdiag).
+// The diagonal of U is folded into K (row q scaled by 1/u_q), so each solve
+// step on the device is one fused multiply-add:
+//     forward   y_q = f'_q - ta_q * y_{q-1},   ta_q = e_{q-1} / u_q
+//     backward  z_q = y_q  - tb_q * z_{q+1},   tb_q = e_q / u_q
+// where e_q = h_q / 6 is the off-diagonal of M_{l-1}.
+#include <cmath>
+#include <cstring>
+
+#include "mgr_internal.h"
+
+namespace mgr {
+namespace {
+
+int64_t coarse_len(int64_t n) { return n / 2 + 1; }  // even positions plus the last one
+
+int levels_until(int64_t n, int64_t stop) {
+  int L = 0;
+  while (n > stop) {
+    n = coarse_len(n);
+    ++L;
+  }
+  return L;
+}
+
+}  // namespace
+
+int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels) {
+  if (!d || d->ndim < 1 || d->ndim > 3) return MGR_EINVAL;
+  int mx = 1 << 30, df = 1 << 30;
+  for (int k = 0; k < d->ndim; ++k) {
+    if (d->shape[k] < 2 || d->shape[k] > (int64_t(1) << 30)) return MGR_EINVAL;
+    mx = std::min(mx, levels_until(d->shape[k], 2));
+    df = std::min(df, levels_until(d->shape[k], 3));
+  }
+  if (max_levels) *max_levels = mx;
+  if (default_levels) *default_levels = df;
+  if (levels) {
+    int L = d->levels < 0 ? df : d->levels;
+    if (L > mx || L > kMaxLevels) return MGR_EINVAL;
+    *levels = L;
+  }
+  return MGR_OK;
+}
+
+int build_plan_tables(mgr_plan* p) {
+  const mgr_desc& d = p->desc;
+  const int L = p->levels;
+  // full-grid coordinates per internal axis (axis kAxes-1 = fastest)
+  std::vector<double> xs[kAxes];
+  const int lead = kAxes - d.ndim;
+  for (int a = 0; a < kAxes; ++a) {
+    if (a < lead) {
+      p->full[a] = 1;
+      xs[a].assign(1, 0.0);
+      continue;
+    }
+    const int k = a - lead;
+    const int64_t N = d.shape[k];
+    p->full[a] = N;
+    xs[a].resize(N);
+    for (int64_t i = 0; i < N; ++i) xs[a][i] = d.coords[k] ? d.coords[k][i] : double(i);
+    for (int64_t i = 1; i < N; ++i)
+      if (!(xs[a][i] > xs[a][i - 1]) || !std::isfinite(xs[a][i])) return MGR_EINVAL;
+    if (!std::isfinite(xs[a][0])) return MGR_EINVAL;
+  }
+  std::vector<double>& T = p->tables.host;
+  T.clear();
+  p->geom.assign(L + 1, LevelGeom{});
+  // level sizes per axis: n_L = N, n_{l-1} = n_l/2 + 1
+  for (int a = 0; a < kAxes; ++a) {
+    int64_t n = p->full[a];
+    for (int l = L; l >= 1; --l) {
+      AxisLevel& ax = p->geom[l].ax[a];
+      ax.N = p->full[a];
+      ax.s = int64_t(1) << (L - l);
+      ax.n = int(n);
+      if (a < lead) {
+        ax.m = 1;
+        ax.active = false;
+      } else {
+        ax.m = int(coarse_len(n));
+        ax.active = true;
+        n = ax.m;
+      }
+    }
+    p->coarsest[a] = n;
+  }
+  auto push = [&](size_t count) {
+    int64_t off = int64_t(T.size());
+    // keep every table 16-byte aligned in both FP64 and FP32 copies
+    size_t padded = (count + 3) & ~size_t(3);
+    T.resize(T.size() + padded, 0.0);
+    return off;
+  };
+  for (int l = L; l >= 1; --l) {
+    for (int a = 0; a < kAxes; ++a) {
+      AxisLevel& ax = p->geom[l].ax[a];
+      const int n = ax.n, m = ax.m;
+      ax.o_wa = push(n);
+      ax.o_wb = push(n);
+      ax.o_k = push(size_t(5) * m);
+      ax.o_ta = push(m);
+      ax.o_tb = push(m);
+      if (!ax.active) {
+        // identity stencil, no solve
+        T[ax.o_k + 2] = 1.0;
+        continue;
+      }
+      // level-l coordinates
+      std::vector<double> x(n);
+      for (int i = 0; i < n; ++i) x[i] = xs[a][std::min<int64_t>(int64_t(i) * ax.s, ax.N - 1)];
+      auto pidx = [&](int q) { return std::min(2 * q, n - 1); };
+      auto coarse = [&](int i) { return (i % 2 == 0) || (i == n - 1); };
+      // interpolation weights of fine nodes (neighbours i-1 and i+1 are coarse)
+      for (int i = 0; i < n; ++i) {
+        if (coarse(i)) continue;
+        const double xa = x[i - 1], xb = x[i + 1], xj = x[i];
+        T[ax.o_wa + i] = (xb - xj) / (xb - xa);
+        T[ax.o_wb + i] = (xj - xa) / (xb - xa);
+      }
+      // P1 mass matrix on level l: sub ml, diag md, super mu
+      std::vector<double> ml(n), md(n), mu(n);
+      for (int j = 0; j < n; ++j) {
+        const double hl = j > 0 ? x[j] - x[j - 1] : 0.0;
+        const double hr = j < n - 1 ? x[j + 1] - x[j] : 0.0;
+        md[j] = (hl + hr) / 3.0;
+        ml[j] = hl / 6.0;
+        mu[j] = hr / 6.0;
+      }
+      // K = P^T M, row q stored at taps (j - pidx(q) + 2)
+      std::vector<double> K(size_t(5) * m, 0.0);
+      auto addK = [&](int q, int j, double v) {
+        const int t = j - pidx(q) + 2;
+        if (t < 0 || t > 4) return false;
+        K[size_t(5) * q + t] += v;
+        return true;
+      };
+      for (int i = 0; i < n; ++i) {
+        int qs[2];
+        double ws[2];
+        int cnt;
+        if (coarse(i)) {
+          qs[0] = (i + 1) / 2;
+          ws[0] = 1.0;
+          cnt = 1;
+        } else {
+          qs[0] = (i - 1) / 2;  // coarse index of i-1 (even)
+          ws[0] = T[ax.o_wa + i];
+          qs[1] = (i + 1) / 2;  // coarse index of i+1 (even, at most n-1)
+          ws[1] = T[ax.o_wb + i];
+          cnt = 2;
+        }
+        for (int c = 0; c < cnt; ++c) {
+          if (i > 0 && !addK(qs[c], i - 1, ws[c] * ml[i])) return MGR_EINVAL;
+          if (!addK(qs[c], i, ws[c] * md[i])) return MGR_EINVAL;
+          if (i < n - 1 && !addK(qs[c], i + 1, ws[c] * mu[i])) return MGR_EINVAL;
+        }
+      }
+      // coarse mass matrix M_{l-1} and its LU factors
+      std::vector<double> xc(m), cd(m), ce(m), u(m);
+      for (int q = 0; q < m; ++q) xc[q] = x[pidx(q)];
+      for (int q = 0; q < m; ++q) {
+        const double hl = q > 0 ? xc[q] - xc[q - 1] : 0.0;
+        const double hr = q < m - 1 ? xc[q + 1] - xc[q] : 0.0;
+        cd[q] = (hl + hr) / 3.0;
+        ce[q] = hr / 6.0;
+      }
+      u[0] = cd[0];
+      for (int q = 1; q < m; ++q) u[q] = cd[q] - (ce[q - 1] / u[q - 1]) * ce[q - 1];
+      for (int q = 0; q < m; ++q) {
+        const double inv = 1.0 / u[q];
+        for (int t = 0; t < 5; ++t) T[ax.o_k + 5 * q + t] = K[size_t(5) * q + t] * inv;
+        T[ax.o_ta + q] = q > 0 ? ce[q - 1] * inv : 0.0;
+        T[ax.o_tb + q] = q < m - 1 ? ce[q] * inv : 0.0;
+      }
+    }
+  }
+  return MGR_OK;
+}
+
+}  // namespace mgr

@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+The paper refactors Gray-Scott reaction-diffusion output (Sec. IV.A), which is
+not available here; it notes that the refactoring time does not depend on the
+values, so seeded synthetic fields of the same shapes stand in for it.  This
+module only generates inputs (fields and coordinates); it contains none of the
+decomposition's arithmetic and serves both the CUDA path and the CPU oracle.
+
+Workloads
+  C1  65^3 FP64, unit spacing: sum of three seeded sines with random wave
+      vectors |k| <= 4 cycles per domain plus N(0, 1e-3) noise.
+  C2  513^3 (2^9+1, Sec. IV.B's kernel size): Gaussian random field with power
+      spectrum |k|^-5/3 synthesised by FFT, normalised to mean 0 / variance 1.
+  C3  1000 x 700 x 300 (not 2^k+1), geometric coordinates h_i = 1.01^i per
+      axis: smooth low-frequency product of cosines plus 32 Gaussian bumps
+      (centres uniform in index space, widths 2..20 cells, N(0,1) amplitudes).
+"""
+import numpy as np
+
+try:
+    import scipy.fft as _fft
+
+    def _rfftn(a):
+        return _fft.rfftn(a, workers=-1)
+
+    def _irfftn(a, s):
+        return _fft.irfftn(a, s=s, workers=-1)
+except Exception:  # pragma: no cover
+    def _rfftn(a):
+        return np.fft.rfftn(a)
+
+    def _irfftn(a, s):
+        return np.fft.irfftn(a, s=s)
+
+
+def uniform_coords(shape):
+    return [np.arange(n, dtype=np.float64) for n in shape]
+
+
+def stretched_coords(n, ratio=1.01, h0=1.0):
+    """x_0 = 0, x_{i+1} - x_i = h0 * ratio**i (formed in FP64)."""
+    return np.concatenate([[0.0], np.cumsum(h0 * ratio ** np.arange(n - 1, dtype=np.float64))])
+
+
+def sines_field(shape, seed=0, n_waves=3, kmax=4.0, noise=1e-3):
+    """C1: sum of seeded sines, wave vectors uniform in the ball |k| <= kmax."""
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    grids = np.meshgrid(*[np.arange(n, dtype=np.float64) / (n - 1) for n in shape], indexing="ij")
+    u = np.zeros(shape)
+    for _ in range(n_waves):
+        while True:
+            k = rng.uniform(-kmax, kmax, d)
+            if np.linalg.norm(k) <= kmax:
+                break
+        phi = rng.uniform(0, 2 * np.pi)
+        u += np.sin(2 * np.pi * sum(k[i] * grids[i] for i in range(d)) + phi)
+    u += rng.normal(0.0, noise, shape)
+    return u
+
+
+def grf_field(shape, seed=0, slope=-5.0 / 3.0):
+    """C2: Gaussian random field with power |k|^slope (amplitude |k|^(slope/2))."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(shape)
+    spec = _rfftn(white)
+    del white
+    d = len(shape)
+    k2 = None
+    for ax in range(d):
+        n = shape[ax]
+        if ax == d - 1:
+            k = np.fft.rfftfreq(n) * n
+        else:
+            k = np.fft.fftfreq(n) * n
+        sh = [1] * d
+        sh[ax] = k.shape[0]
+        term = (k.reshape(sh)) ** 2
+        k2 = term if k2 is None else k2 + term
+    with np.errstate(divide="ignore"):
+        amp = np.where(k2 > 0, k2 ** (slope / 4.0), 0.0)
+    spec *= amp
+    del amp, k2
+    u = _irfftn(spec, s=shape)
+    del spec
+    u -= u.mean()
+    u /= u.std()
+    return u
+
+
+def bumps_field(shape, seed=0, n_bumps=32, coords=None):
+    """C3: smooth product of cosines over normalised coordinates plus Gaussian bumps."""
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    if coords is None:
+        coords = [stretched_coords(n) for n in shape]
+    xn = [(c - c[0]) / (c[-1] - c[0]) for c in coords]
+    freqs = rng.uniform(0.5, 2.0, d)
+    phases = rng.uniform(0, 2 * np.pi, d)
+    smooth = [np.cos(2 * np.pi * freqs[k] * xn[k] + phases[k]) for k in range(d)]
+    centres = [rng.uniform(0, shape[k] - 1, n_bumps) for k in range(d)]
+    widths = rng.uniform(2.0, 20.0, n_bumps)
+    amps = rng.standard_normal(n_bumps)
+    idx = [np.arange(n, dtype=np.float64) for n in shape]
+    # separable factors: g[k][b, i] = exp(-((i - c_b)/sigma_b)^2 / 2)
+    g = [np.exp(-0.5 * ((idx[k][None, :] - centres[k][:, None]) / widths[:, None]) ** 2) for k in range(d)]
+    out = np.empty(shape, dtype=np.float64)
+    if d == 1:
+        out[:] = smooth[0] + (amps[:, None] * g[0]).sum(0)
+        return out
+    rest_shape = shape[1:]
+    # rest[b, ...] = outer product of the factors of axes 1..d-1 for bump b
+    rest = g[1]
+    for k in range(2, d):
+        rest = (rest[:, :, None] * g[k][:, None, :]).reshape(n_bumps, -1)
+    rest = rest.reshape(n_bumps, -1)
+    smooth_rest = smooth[1]
+    for k in range(2, d):
+        smooth_rest = np.multiply.outer(smooth_rest, smooth[k])
+    smooth_rest = smooth_rest.reshape(-1)
+    lead = (amps[:, None] * g[0]).T  # (n0, n_bumps)
+    chunk = max(1, int(2 ** 26 // max(1, rest.shape[1])))
+    flat = out.reshape(shape[0], -1)
+    for i0 in range(0, shape[0], chunk):
+        i1 = min(shape[0], i0 + chunk)
+        flat[i0:i1] = lead[i0:i1] @ rest
+        flat[i0:i1] += smooth[0][i0:i1, None] * smooth_rest[None, :]
+    return out
+
+
+WORKLOADS = {
+    "c1": dict(shape=(65, 65, 65), dtype="f64", coords="uniform"),
+    "c2": dict(shape=(513, 513, 513), dtype="f64", coords="uniform"),
+    "c3": dict(shape=(1000, 700, 300), dtype="f32", coords="stretched"),
+}
+
+
+def workload(name, seed=0, shape=None):
+    """(field, coords) of a named workload; coords is None for unit spacing."""
+    spec = WORKLOADS[name]
+    shape = tuple(shape) if shape is not None else spec["shape"]
+    if name == "c1":
+        return sines_field(shape, seed), None
+    if name == "c2":
+        return grf_field(shape, seed), None
+    coords = [stretched_coords(n) for n in shape]
+    return bumps_field(shape, seed, coords=coords), coords
