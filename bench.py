@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Refactoring throughput of multigrid decomposition + recomposition on one GB300.
+
+One step = decompose + recompose of the 513^3 field (the full hot path: every
+level's coefficients, mass-transfer stencils, tridiagonal solves and
+correction, then the inverse).  The headline `value` is the plain FP64 form:
+refactor GB/s = 2 x input bytes / (t_decompose + t_recompose).  The FP32 and
+mixed-precision forms of the same field are reported under "forms".
+
+Multi-GPU: a single field does not shard, so N > 1 runs N independent replicas
+(one field per GPU, no data-path collective); `value` sums their bytes over the
+slowest rank's time (weak scaling).
+
+--impl reference times the FP64 CPU oracle instead (the reference arm of this
+build: a plain, single-threaded CPU implementation), on a bounded sample.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (513, 513, 513)
+METRIC = "refactor GB/s (decomp+recomp) & % HBM peak vs plain FP64"
+UNIT = "GB/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (the recipe's
+# 1.25 TFLOP/s FP64 figure); a DFMA microbenchmark measured 1.196 TFLOP/s at
+# the ~1.99 GHz clock it ran at.
+FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--shape", default=None, help="override, e.g. 257,257,257")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def path_bytes(shape, levels, elem):
+    """Algorithmic bytes of one decomposition: 2 * s * sum_l n_l (read every
+    level grid once, write its coefficients and coarse grid once)."""
+    n = list(shape)
+    total = 0
+    for _ in range(levels):
+        c = 1
+        for v in n:
+            c *= v
+        total += c
+        n = [v // 2 + 1 for v in n]
+    return 2.0 * elem * total
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        inside = [p for (t, p) in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(inside) < 3:
+            inside = [p for (_, p) in self.samples]
+            window = "warm-up + timed region (timed region shorter than 3 samples)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4) if p[3 + i].lower().startswith("active")})
+        sm = [float(p[0]) for p in inside if p[0].replace(".", "").isdigit()]
+        mx = [float(p[1]) for p in inside if p[1].replace(".", "").isdigit()]
+        pw = [float(p[2]) for p in inside if p[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(inside), "window": window}
+
+
+# ----------------------------------------------------------------- helpers --
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_field(shape, seed):
+    from paper_2105_12764_gb300 import synth
+
+    return synth.grf_field(shape, seed)
+
+
+def traffic_for(kernel, shape_key, src_hash):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(f"{kernel}@{shape_key}")
+        if e and e.get("source_sha1") == src_hash:
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def core_source_hash():
+    h = hashlib.sha1()
+    for name in ("mgr_core.cu",):
+        with open(os.path.join(ROOT, "paper_2105_12764_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+# ---------------------------------------------------------------- our arm ---
+
+def time_form(mgr, ctx, u_np, dtype, prec, steps, warmup, ws, sampler=None):
+    import numpy as np
+    import torch
+
+    td = torch.float64 if dtype == mgr.MGR_F64 else torch.float32
+    nd = np.float64 if dtype == mgr.MGR_F64 else np.float32
+    plan = mgr.Plan(ctx, u_np.shape, None, -1, dtype, prec)
+    x = torch.from_numpy(np.ascontiguousarray(u_np, dtype=nd)).cuda()
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    wsb = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.decompose(x, y, wsb, st)
+        plan.recompose(y, z, wsb, st)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(steps):
+        ev[i][0].record(st)
+        plan.decompose(x, y, wsb, st)
+        ev[i][1].record(st)
+        plan.recompose(y, z, wsb, st)
+        ev[i][2].record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t1 = time.time()
+    t_dec = sum(a.elapsed_time(b) for a, b, _ in ev) / steps
+    t_rec = sum(b.elapsed_time(c) for _, b, c in ev) / steps
+    # correctness of what was timed: round trip of the last step
+    rt = float((z - x).abs().max().item() / x.abs().max().item())
+    return plan, (x, y, z, wsb), t_dec, t_rec, rt, (t0, t1)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2105_12764_gb300 as mgr
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else SHAPE
+    peaks, peak_src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    u = make_field(shape, seed=rank)
+    ctx = mgr.Context(local)
+    nbytes64 = u.size * 8
+    sampler = ClockSampler(local)
+    sampler.start()
+    plan, bufs, t_dec, t_rec, rt64, (t0, t1) = time_form(mgr, ctx, u, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, args.steps,
+                                                           args.warmup, ws)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    step_ms = max_over_ranks(t_dec + t_rec, ws)
+    value = ws * 2.0 * nbytes64 / (step_ms * 1e-3) / 1e9
+    L = plan.levels
+    alg = path_bytes(shape, L, 8)
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded k^-5/3 Gaussian random field (FFT), unit variance",
+        "config": {"workload": f"{'x'.join(map(str, shape))} uniform grid, FP64, full hierarchy ({L} levels), "
+                               "decompose + recompose per step", "shape": list(shape), "levels": L,
+                   "l2": "inputs larger than L2 (field 1.08 GB vs 129 MB L2); no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "decompose_gbs": round(nbytes64 / (t_dec * 1e-3) / 1e9, 3),
+        "recompose_gbs": round(nbytes64 / (t_rec * 1e-3) / 1e9, 3),
+        "hbm_frac_alg": round(2.0 * alg / ((t_dec + t_rec) * 1e-3) / 1e9 / hbm, 4),
+        "round_trip_rel_err": rt64,
+        "clocks": clocks,
+    }
+    # ---- per-kernel CUDA-event timing of the same operation (dominant kernel roofline)
+    x, y, z, wsb = bufs
+    prof_steps = max(1, min(5, args.steps))
+    agg = {}
+    launches = 0
+    for _ in range(prof_steps):
+        for op, (src, dst) in ((0, (x, y)), (1, (y, z))):
+            recs = plan.profile(op, src, dst, wsb)
+            if _ == 0:
+                launches += len(recs)
+            for r in recs:
+                key = (r["name"], r["level"])
+                a = agg.setdefault(key, [0.0, 0, r["bytes"], r["flops"]])
+                a[0] += r["ms"]
+                a[1] += 1
+    total_ms = sum(a[0] for a in agg.values())
+    (dname, dlevel), dom = max(agg.items(), key=lambda kv: kv[1][0])
+    dom_ms = dom[0] / dom[1]
+    ach_gbs = dom[2] / (dom_ms * 1e-3) / 1e9
+    ach_tflops = dom[3] / (dom_ms * 1e-3) / 1e12
+    frac_hbm = ach_gbs / hbm
+    frac_alu = ach_tflops / FP64_ALU_TFLOPS
+    src_hash = core_source_hash()
+    traffic = traffic_for(dname, "x".join(map(str, shape)) + ":f64", src_hash)
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": round(ach_tflops, 4), "peak": round(FP64_ALU_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": traffic,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(ach_gbs, 2), "peak": hbm, "unit": "GB/s", "frac": round(frac_hbm, 4),
+                "traffic": traffic, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    roof.update({"kernel": f"{dname} (level {dlevel})", "kernel_ms": round(dom_ms, 4),
+                 "share": round(dom[0] / total_ms, 4), "alg_bytes_per_launch": dom[2],
+                 "alg_flops_per_launch": dom[3], "hbm_frac_same_kernel": round(frac_hbm, 4)})
+    result["roofline"] = roof
+    result["gpu_launches"] = launches * args.steps
+    result["kernels"] = {f"{k[0]}@L{k[1]}": round(v[0] / v[1], 4) for k, v in
+                         sorted(agg.items(), key=lambda kv: -kv[1][0])[:12]}
+    # ---- end-to-end through the C ABI with host buffers
+    pin_in = torch.from_numpy(u.astype(np.float64)).pin_memory()
+    pin_c = torch.empty_like(pin_in).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    st = torch.cuda.current_stream()
+    e_steps = max(1, min(args.steps, 10))
+    for _ in range(2):
+        plan.decompose_host(pin_in, pin_c, x, y, wsb, st)
+        plan.recompose_host(pin_c, pin_out, y, z, wsb, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    e0.record(st)
+    for _ in range(e_steps):
+        plan.decompose_host(pin_in, pin_c, x, y, wsb, st)
+        plan.recompose_host(pin_c, pin_out, y, z, wsb, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, ws)
+    e_rt = float(np.abs(pin_out.numpy() - u).max() / np.abs(u).max())
+    result["e2e"] = {"value": round(ws * 2.0 * nbytes64 / (e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+                     "h2d_bytes_per_step": 2 * nbytes64, "d2h_bytes_per_step": 2 * nbytes64,
+                     "ms_per_step": round(e_ms, 4), "round_trip_rel_err": e_rt,
+                     "path": "mgr_decompose_host + mgr_recompose_host, pinned host buffers"}
+    del pin_in, pin_c, pin_out
+    plan.close()
+    del bufs, x, y, z, wsb
+    torch.cuda.empty_cache()
+    # ---- FP32 and mixed forms of the same field
+    if not args.no_forms:
+        forms = {}
+        for name, prec in (("fp32", mgr.MGR_PREC_NATIVE), ("mixed", mgr.MGR_PREC_MIXED)):
+            p2, b2, td, tr, rt, _ = time_form(mgr, ctx, u.astype(np.float32), mgr.MGR_F32, prec,
+                                              max(3, args.steps), args.warmup, ws)
+            nb = u.size * 4
+            alg4 = path_bytes(shape, p2.levels, 4)
+            forms[name] = {"value": round(2.0 * nb / ((td + tr) * 1e-3) / 1e9, 3), "unit": UNIT,
+                           "decompose_gbs": round(nb / (td * 1e-3) / 1e9, 3),
+                           "recompose_gbs": round(nb / (tr * 1e-3) / 1e9, 3),
+                           "ms_per_step": round(td + tr, 4),
+                           "hbm_frac_alg": round(2.0 * alg4 / ((td + tr) * 1e-3) / 1e9 / hbm, 4),
+                           "speedup_vs_fp64": round((t_dec + t_rec) / (td + tr), 3),
+                           "round_trip_rel_err": rt}
+            p2.close()
+            del b2
+            torch.cuda.empty_cache()
+        result["forms"] = forms
+    # ---- CPU baseline: the FP64 oracle, single thread, on rank 0 at N = 1
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(u)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def cpu_baseline(u):
+    import oracle
+
+    t = time.time()
+    c = oracle.decompose(u)
+    t_dec = time.time() - t
+    t = time.time()
+    oracle.recompose(c)
+    t_rec = time.time() - t
+    return {"value": round(2.0 * u.nbytes / (t_dec + t_rec) / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one decompose + recompose of the full {'x'.join(map(str, u.shape))} FP64 field "
+                      f"({t_dec + t_rec:.1f} s)"}
+
+
+# ------------------------------------------------------- reference arm -----
+
+def run_reference(args):
+    import numpy as np
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else SHAPE
+    u_full = make_field(shape, seed=0)
+    # bounded sample: the 257^3 corner block of the field (a few s per step)
+    sub = tuple(min(257, s) for s in shape)
+    u = np.ascontiguousarray(u_full[:sub[0], :sub[1], :sub[2]])
+    del u_full
+    for _ in range(args.warmup):
+        oracle.recompose(oracle.decompose(u))
+    t = time.time()
+    for _ in range(args.steps):
+        oracle.recompose(oracle.decompose(u))
+    dt = (time.time() - t) / args.steps
+    value = 2.0 * u.nbytes / dt / 1e9
+    sample = f"{'x'.join(map(str, sub))} corner block of the {'x'.join(map(str, shape))} FP64 field per step"
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "impl": "reference", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded k^-5/3 GRF",
+           "config": {"workload": f"{'x'.join(map(str, shape))} uniform grid, FP64, full hierarchy, decompose + "
+                                  "recompose per step (CPU oracle on a bounded sample)", "shape": list(shape)},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,27 @@ int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out
 int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
                        void* workspace, mgr_stream_t stream);
 
+/* ------------------------------------------------------------ profiling */
+
+/* One kernel launch of an operation, timed by CUDA events recorded on the
+   launching stream immediately before and after it. */
+typedef struct {
+  char name[32]; /* kernel role: level_load_dec, level_load_rec, solve_x/y/z, interp,
+                    coarsest, coef_inplace                                          */
+  int level;     /* level l of the launch (0 for the coarsest-grid copy)            */
+  float ms;      /* event-to-event duration                                         */
+  double bytes;  /* compulsory bytes of the launch's inputs and outputs             */
+  double flops;  /* floating-point operations of its minimal arithmetic (FMA = 2)   */
+} mgr_kernel_time;
+
+/* Run one decomposition (op = 0) or recomposition (op = 1) exactly as
+   mgr_decompose / mgr_recompose would, but launched directly (no graph) with
+   a pair of CUDA events around every kernel, and wait for it.  Writes up to
+   `cap` records to `times` and the number of launches to *n (which may exceed
+   cap).  Not part of the hot path: it synchronises `stream`. */
+int mgr_profile(const mgr_plan* plan, int op, const void* in, void* out, void* workspace, mgr_stream_t stream,
+                mgr_kernel_time* times, int cap, int* n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ import os
 __all__ = [
     "MGR_OK", "MGR_EINVAL", "MGR_ENOMEM", "MGR_EBUDGET", "MGR_ECUDA", "MGR_EPENDING", "MGR_ETIMEDOUT",
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
-    "MgrError", "mgr_desc", "lib", "library_path", "Context", "Plan", "EXPORTED",
+    "MgrError", "mgr_desc", "mgr_kernel_time", "lib", "library_path", "Context", "Plan", "EXPORTED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +44,16 @@ class mgr_desc(ctypes.Structure):
     ]
 
 
+class mgr_kernel_time(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("level", ctypes.c_int),
+        ("ms", ctypes.c_float),
+        ("bytes", ctypes.c_double),
+        ("flops", ctypes.c_double),
+    ]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 # name -> (restype, argtypes): every entry point declared in include/mgr.h
@@ -62,6 +72,7 @@ EXPORTED = {
     "mgr_recompose": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mgr_decompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
 }
 
 
@@ -186,6 +197,15 @@ class Plan:
     def recompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
         _check("mgr_recompose_host", lib.mgr_recompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),
                                                             _ptr(dev_out), _ptr(workspace), _stream(stream)))
+
+    def profile(self, op, inp, out, workspace, stream=None, cap=512):
+        """mgr_profile: list of dicts (name, level, ms, bytes, flops), one per kernel launch."""
+        arr = (mgr_kernel_time * cap)()
+        n = _i()
+        _check("mgr_profile", lib.mgr_profile(self.handle, int(op), _ptr(inp), _ptr(out), _ptr(workspace),
+                                              _stream(stream), arr, cap, ctypes.byref(n)))
+        return [dict(name=arr[i].name.decode(), level=arr[i].level, ms=arr[i].ms, bytes=arr[i].bytes,
+                     flops=arr[i].flops) for i in range(min(n.value, cap))]
 
     def close(self):
         if self.handle:

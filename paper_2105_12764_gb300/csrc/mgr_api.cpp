@@ -278,4 +278,38 @@ int mgr_recompose_host(const mgr_plan* p, const void* host_in, void* host_out, v
   return run_host(p, OP_REC, host_in, host_out, dev_in, dev_out, ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int mgr_profile(const mgr_plan* p, int op, const void* in, void* out, void* ws, mgr_stream_t stream,
+                mgr_kernel_time* times, int cap, int* n) {
+  if (!n || (cap > 0 && !times) || (op != OP_DEC && op != OP_REC)) return MGR_EINVAL;
+  int rc = check_op_args(p, in, out, ws);
+  if (rc != MGR_OK) return rc;
+  if ((rc = check_sticky()) != MGR_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  mgr::Recorder rec;
+  mgr::t_recorder = &rec;
+  cudaError_t e = enqueue(p, op, in, out, ws, st);
+  mgr::t_recorder = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *n = int(rec.launches.size());
+  for (size_t i = 0; i < rec.launches.size(); ++i) {
+    mgr::LaunchRecord& r = rec.launches[i];
+    float ms = 0.f;
+    if (e == cudaSuccess && r.stop) cudaEventElapsedTime(&ms, r.start, r.stop);
+    if (int(i) < cap) {
+      std::memcpy(times[i].name, r.name, sizeof(times[i].name));
+      times[i].level = r.level;
+      times[i].ms = ms;
+      times[i].bytes = r.bytes;
+      times[i].flops = r.flops;
+    }
+    cudaEventDestroy(r.start);
+    if (r.stop) cudaEventDestroy(r.stop);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ECUDA;
+  }
+  return MGR_OK;
+}
+
 }  // extern "C"

@@ -29,11 +29,34 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 
 #include "mgr_internal.h"
 
 namespace mgr {
+
+thread_local Recorder* t_recorder = nullptr;
+
 namespace {
+
+// Optional per-launch CUDA-event instrumentation (mgr_profile).
+inline void rec_begin(cudaStream_t st) {
+  if (!t_recorder) return;
+  LaunchRecord r{};
+  cudaEventCreate(&r.start);
+  cudaEventCreate(&r.stop);
+  cudaEventRecord(r.start, st);
+  t_recorder->launches.push_back(r);
+}
+inline void rec_end(cudaStream_t st, const char* name, int level, double bytes, double flops) {
+  if (!t_recorder) return;
+  LaunchRecord& r = t_recorder->launches.back();
+  cudaEventRecord(r.stop, st);
+  std::snprintf(r.name, sizeof(r.name), "%s", name);
+  r.level = level;
+  r.bytes = bytes;
+  r.flops = flops;
+}
 
 constexpr int BX = 32;   // coarse x nodes per CTA tile (one warp across x)
 constexpr int BY = 8;    // coarse y nodes per CTA tile
@@ -550,7 +573,20 @@ dim3 load_grid(const mgr_plan* p, LoadArgs<TS, TW>& a) {
 }
 
 template <typename TW>
+cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st);
+
+template <typename TW>
 cudaError_t solve_axis(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st) {
+  const Work wk = work_solve(p, l, axis, op != SOLVE_INPLACE);
+  static const char* names[3] = {"solve_z", "solve_y", "solve_x"};
+  rec_begin(st);
+  cudaError_t err = solve_axis_launch<TW>(p, l, axis, f, w, op, st);
+  rec_end(st, names[axis], l, wk.bytes, wk.flops);
+  return err;
+}
+
+template <typename TW>
+cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st) {
   const LevelGeom& g = p->geom[l];
   const int mz = g.ax[0].m, my = g.ax[1].m, mx = g.ax[2].m;
   const TW* T = table<TW>(p);
@@ -638,6 +674,7 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
       a.in_sy = a.y_sy;
       constexpr size_t sm = load_smem_bytes<TD, TS>();
       cudaFuncSetAttribute(k_level_load<MODE_DEC, TD, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      rec_begin(st);
       k_level_load<MODE_DEC, TD, TD, TS, TW><<<grid, block, sm, st>>>(a);
     } else {
       const LevelGeom& g = p->geom[l];
@@ -647,18 +684,29 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
       a.in_sy = g.ax[2].n;
       constexpr size_t sm = load_smem_bytes<TW, TS>();
       cudaFuncSetAttribute(k_level_load<MODE_DEC, TW, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      rec_begin(st);
       k_level_load<MODE_DEC, TW, TD, TS, TW><<<grid, block, sm, st>>>(a);
     }
     cudaError_t e = cudaGetLastError();
+    {
+      const Work wk = work_level_load(p, l, true);
+      rec_end(st, "level_load_dec", l, wk.bytes, wk.flops);
+    }
     if (e != cudaSuccess) return e;
     if (l == L && inplace) {
       const LevelGeom& g = p->geom[l];
       const TS* T = table<TS>(p);
       const int64_t total = g.fine_count();
+      rec_begin(st);
       k_coef_inplace<TD, TS><<<grid_1d(total, 256, p), 256, 0, st>>>(
           static_cast<TD*>(out), g.ax[0].n, g.ax[1].n, g.ax[2].n, T + g.ax[0].o_wa, T + g.ax[0].o_wb,
           T + g.ax[1].o_wa, T + g.ax[1].o_wb, T + g.ax[2].o_wa, T + g.ax[2].o_wb);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      e = cudaGetLastError();
+      {
+        const Work wi = work_interp(p, l);
+        rec_end(st, "coef_inplace", l, 2.0 * double(total) * sizeof(TD), wi.flops);
+      }
+      if (e != cudaSuccess) return e;
     }
     if ((e = solve_level<TW>(p, l, F, nxt, SOLVE_ADD, st)) != cudaSuccess) return e;
     cur = nxt;
@@ -669,9 +717,12 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
   const longlong3 N = make_longlong3(p->full[0], p->full[1], p->full[2]);
   const int64_t total = int64_t(n0.x) * n0.y * n0.z;
+  rec_begin(st);
   k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(static_cast<TD*>(out), p->full[1] * p->full[2],
                                                                p->full[2], cur, n0, s, N, 1);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
+  return e;
 }
 
 template <typename TD, typename TS, typename TW>
@@ -692,9 +743,11 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
     const longlong3 N = make_longlong3(p->full[0], p->full[1], p->full[2]);
     const int64_t total = int64_t(n0.x) * n0.y * n0.z;
+    rec_begin(st);
     k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(const_cast<TD*>(static_cast<const TD*>(in)),
                                                                  p->full[1] * p->full[2], p->full[2], cur, n0, s, N, 0);
     cudaError_t e = cudaGetLastError();
+    rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
     if (e != cudaSuccess) return e;
   }
   for (int l = 1; l <= L; ++l) {
@@ -711,8 +764,13 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     dim3 block(BX, BY);
     constexpr size_t sm = load_smem_bytes<TD, TS>();
     cudaFuncSetAttribute(k_level_load<MODE_REC, TD, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    rec_begin(st);
     k_level_load<MODE_REC, TD, TD, TS, TW><<<grid, block, sm, st>>>(a);
     cudaError_t e = cudaGetLastError();
+    {
+      const Work wk = work_level_load(p, l, false);
+      rec_end(st, "level_load_rec", l, wk.bytes, wk.flops);
+    }
     if (e != cudaSuccess) return e;
     if ((e = solve_level<TW>(p, l, F, cur, SOLVE_SUB, st)) != cudaSuccess) return e;
     const LevelGeom& g = p->geom[l];
@@ -722,6 +780,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     const longlong3 N = make_longlong3(g.ax[0].N, g.ax[1].N, g.ax[2].N);
     const int64_t total = g.fine_count();
     const int64_t c_sz = int64_t(g.ax[1].m) * g.ax[2].m, c_sy = g.ax[2].m;
+    rec_begin(st);
     if (l == L) {
       k_interp<TD, TD, TS, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(
           static_cast<const TD*>(in), a.y_sz, a.y_sy, n, s, N, cur, c_sz, c_sy, static_cast<TD*>(out), a.y_sz, a.y_sy,
@@ -733,7 +792,12 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
           T + g.ax[0].o_wa, T + g.ax[0].o_wb, T + g.ax[1].o_wa, T + g.ax[1].o_wb, T + g.ax[2].o_wa, T + g.ax[2].o_wb);
       cur = nxt;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaGetLastError();
+    {
+      const Work wk = work_interp(p, l);
+      rec_end(st, "interp", l, wk.bytes, wk.flops);
+    }
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -95,6 +95,27 @@ struct mgr_plan {
 
 namespace mgr {
 
+// Per-launch instrumentation used by mgr_profile (events around every launch).
+struct LaunchRecord {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  char name[32] = {0};
+  int level = 0;
+  double bytes = 0, flops = 0;
+};
+struct Recorder {
+  std::vector<LaunchRecord> launches;
+};
+extern thread_local Recorder* t_recorder;
+
+// Algorithmic work of one launch: compulsory bytes and floating-point
+// operations (fused multiply-add = 2) of the arithmetic the kernel must do.
+struct Work {
+  double bytes = 0, flops = 0;
+};
+Work work_level_load(const mgr_plan* p, int l, bool decompose);
+Work work_solve(const mgr_plan* p, int l, int axis, bool final_op);
+Work work_interp(const mgr_plan* p, int l);
+
 // mgr_plan.cpp
 int build_plan_tables(mgr_plan* p);
 int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels);

@@ -191,3 +191,89 @@ int build_plan_tables(mgr_plan* p) {
 }
 
 }  // namespace mgr
+
+// ---------------------------------------------------------------------------
+// Algorithmic work per launch (reported by mgr_profile).
+//
+// Flop counts are those of the minimal arithmetic of each step, counting a
+// fused multiply-add as 2 flops:
+//   coefficients / interpolant, separable form: a node whose slowest fine axis
+//     is k costs 3 FMA (interpolate along k, keep that value for the slower
+//     axes, subtract) or 2 FMA when k is the slowest active axis;
+//   mass-transfer along x: 5 taps per coarse output, 2 on lines whose other
+//     coordinates are all coarse (the coefficients vanish on coarse nodes);
+//   along y and z: 5 taps per output; solves: 2 FMA per coarse node and axis.
+// Bytes are the compulsory traffic of each launch's inputs and outputs.
+// ---------------------------------------------------------------------------
+namespace mgr {
+namespace {
+
+double coef_fma(const LevelGeom& g) {
+  int slowest = -1;
+  for (int k = 0; k < kAxes; ++k)
+    if (g.ax[k].active) { slowest = k; break; }
+  double total = 0;
+  for (int k = 0; k < kAxes; ++k) {
+    if (!g.ax[k].active) continue;
+    // nodes whose slowest fine axis is k: coarse on slower axes (j < k),
+    // fine on k, anything on faster axes (j > k)
+    double cnt = double(g.ax[k].n - g.ax[k].m);
+    for (int j = 0; j < k; ++j) cnt *= g.ax[j].m;
+    for (int j = k + 1; j < kAxes; ++j) cnt *= g.ax[j].n;
+    total += cnt * (k == slowest ? 2.0 : 3.0);
+  }
+  return total;
+}
+
+double stencil_fma(const LevelGeom& g) {
+  const AxisLevel &z = g.ax[0], &y = g.ax[1], &x = g.ax[2];
+  double t = 0;
+  if (x.active) {
+    const double lines_coarse = double(z.m) * y.m;
+    const double lines_all = double(z.n) * y.n;
+    t += x.m * (2.0 * lines_coarse + 5.0 * (lines_all - lines_coarse));
+  }
+  if (y.active) t += 5.0 * double(z.n) * y.m * x.m;
+  if (z.active) t += 5.0 * double(z.m) * y.m * x.m;
+  return t;
+}
+
+}  // namespace
+
+Work work_level_load(const mgr_plan* p, int l, bool decompose) {
+  const LevelGeom& g = p->geom[l];
+  const double n = double(g.fine_count()), m = double(g.coarse_count());
+  const double sd = double(p->elem), sw = double(p->welem);
+  Work w;
+  if (decompose) {
+    const double sin = (l == p->levels) ? sd : sw;
+    w.bytes = n * sin + (n - m) * sd + 2.0 * m * sw;
+    w.flops = 2.0 * (coef_fma(g) + stencil_fma(g));
+  } else {
+    w.bytes = n * sd + m * sw;
+    w.flops = 2.0 * stencil_fma(g);
+  }
+  return w;
+}
+
+Work work_solve(const mgr_plan* p, int l, int axis, bool final_op) {
+  (void)axis;
+  const double m = double(p->geom[l].coarse_count());
+  const double sw = double(p->welem);
+  Work w;
+  w.bytes = 2.0 * m * sw + (final_op ? 2.0 * m * sw : 0.0);
+  w.flops = 4.0 * m + (final_op ? m : 0.0);
+  return w;
+}
+
+Work work_interp(const mgr_plan* p, int l) {
+  const LevelGeom& g = p->geom[l];
+  const double n = double(g.fine_count()), m = double(g.coarse_count());
+  const double sd = double(p->elem), sw = double(p->welem);
+  Work w;
+  w.bytes = n * sd + m * sw + n * (l == p->levels ? sd : sw);
+  w.flops = 2.0 * coef_fma(g);
+  return w;
+}
+
+}  // namespace mgr

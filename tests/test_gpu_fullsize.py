@@ -1,0 +1,82 @@
+"""Full-size parity: the bench workloads through the C ABI vs the FP64 oracle.
+
+C2: 513^3 k^-5/3 field, full hierarchy (8 levels), in the launch
+configuration bench.py times (same plan, graph-replayed launches):
+  FP64 vs oracle <= 1e-12, round trip <= 1e-13; FP32 and mixed <= 1e-5.
+C3: 1000 x 700 x 300 stretched (1.01 per cell), mixed precision <= 1e-5.
+Every output element is compared (the oracle computes the whole field).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_12764_gb300 as mgr
+from gpu_util import Runner, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return mgr.Context(0)
+
+
+@pytest.fixture(scope="module")
+def c2_field():
+    from paper_2105_12764_gb300 import synth
+
+    return synth.workload("c2")[0]
+
+
+@pytest.fixture(scope="module")
+def c2_oracle(c2_field):
+    return oracle.decompose(c2_field)
+
+
+def test_c2_fp64_full(ctx, c2_field, c2_oracle):
+    r = Runner(ctx, c2_field.shape, None, -1, mgr.MGR_F64)
+    try:
+        got = r.decompose(c2_field)
+        assert rel_linf(got, c2_oracle) <= 1e-12
+        back = r.recompose(got)
+        assert rel_linf(back, c2_field) <= 1e-13
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("prec", [mgr.MGR_PREC_NATIVE, mgr.MGR_PREC_MIXED])
+def test_c2_fp32_forms_full(ctx, c2_field, prec):
+    u32 = c2_field.astype(np.float32)
+    ref = oracle.decompose(u32.astype(np.float64))
+    r = Runner(ctx, c2_field.shape, None, -1, mgr.MGR_F32, prec)
+    try:
+        got = r.decompose(u32)
+        err = rel_linf(got, ref)
+        assert err <= 1e-5, err
+        back = r.recompose(got)
+        assert rel_linf(back, u32) <= 1e-5
+    finally:
+        r.close()
+
+
+def test_c3_mixed_full(ctx):
+    from paper_2105_12764_gb300 import synth
+
+    u, coords = synth.workload("c3")
+    u32 = u.astype(np.float32)
+    del u
+    ref = oracle.decompose(u32.astype(np.float64), coords)
+    r = Runner(ctx, u32.shape, coords, -1, mgr.MGR_F32, mgr.MGR_PREC_MIXED)
+    try:
+        assert r.plan.levels == 8
+        got = r.decompose(u32)
+        err = rel_linf(got, ref)
+        assert err <= 1e-5, err
+        back = r.recompose(got)
+        assert rel_linf(back, u32) <= 1e-5
+    finally:
+        r.close()
