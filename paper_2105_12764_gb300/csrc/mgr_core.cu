@@ -58,14 +58,6 @@ inline void rec_end(cudaStream_t st, const char* name, int level, double bytes, 
   r.flops = flops;
 }
 
-constexpr int BX = 32;   // coarse x nodes per CTA tile (one warp across x)
-constexpr int BY = 8;    // coarse y nodes per CTA tile
-constexpr int NT = BX * BY;
-constexpr int RXMAX = 2 * BX + 3;  // fine region width incl. halo (5-tap stencil)
-constexpr int RYMAX = 2 * BY + 3;
-constexpr int RXP = RXMAX + 1;     // shared-memory row pitch
-constexpr int PLANE = RYMAX * RXP;
-
 __device__ __forceinline__ int pidx(int q, int n) { return min(2 * q, n - 1); }
 __device__ __forceinline__ bool is_coarse(int i, int n) { return ((i & 1) == 0) || (i == n - 1); }
 __device__ __forceinline__ int cidx(int i) { return (i + 1) >> 1; }
@@ -79,9 +71,13 @@ __device__ __forceinline__ int64_t fmap(int i, int64_t s, int64_t N) {
   return f < N - 1 ? f : N - 1;
 }
 
+// Asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses
+// aligned to the copy size).
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
   unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if (bytes == 8)
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else if (bytes == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -92,239 +88,7 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// ---------------------------------------------------------------------------
-// k_level_load
-// ---------------------------------------------------------------------------
-
-template <typename TS, typename TW>
-struct LoadArgs {
-  const void* in;      // DEC: level-l values; REC: nodal coefficients (full grid)
-  int64_t in_sz, in_sy;
-  int in_full;         // 1: index `in` through the full-grid map min(i*s, N-1)
-  void* y;             // DEC: nodal output (full grid)
-  int64_t y_sz, y_sy;
-  TW* w;               // DEC: coarse nodal values (compact m grid)
-  TW* f;               // load vector (compact m grid)
-  int64_t c_sz, c_sy;
-  int n[3], m[3];
-  int64_t s[3], N[3];
-  const TS* wa[3];
-  const TS* wb[3];
-  const TS* k[3];
-  int qz_chunk;
-  int write_y;
-};
-
-enum { MODE_DEC = 0, MODE_REC = 1 };
-
-template <int MODE, typename TI, typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(NT, 2) k_level_load(const LoadArgs<TS, TW> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TI* raw = reinterpret_cast<TI*>(smem_raw);                        // [2 stages][2 planes][PLANE]
-  TS* Ibuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * 4 * PLANE);  // [2][PLANE]
-  TS* cb = Ibuf + 2 * PLANE;                                          // [PLANE]
-  TS* gxb = cb + PLANE;                                               // [RYMAX][BX]
-
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
-  const int mz = a.m[0], my = a.m[1], mx = a.m[2];
-  const int qx0 = blockIdx.x * BX, qx1 = min(qx0 + BX, mx);
-  const int qy0 = blockIdx.y * BY, qy1 = min(qy0 + BY, my);
-  const int qz0 = blockIdx.z * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
-  // the region starts on a coarse node so every fine node in it has both
-  // interpolation neighbours inside; pidx(q0) - 2 is fine only in the
-  // keep-last case (q0 = m-1, n even), where one more node is taken
-  const int rx0 = max(region_start(qx0, nx), 0), rx1 = min(pidx(qx1 - 1, nx) + 2, nx - 1);
-  const int ry0 = max(region_start(qy0, ny), 0), ry1 = min(pidx(qy1 - 1, ny) + 2, ny - 1);
-  const int RX = rx1 - rx0 + 1, RY = ry1 - ry0 + 1, RE = RX * RY;
-  // owned fine ranges (each fine node is written by exactly one CTA)
-  const int ox0 = pidx(qx0, nx), ox1 = (qx1 == mx) ? nx : pidx(qx1, nx);
-  const int oy0 = pidx(qy0, ny), oy1 = (qy1 == my) ? ny : pidx(qy1, ny);
-  // first coarse plane streamed: the one before the chunk, or two before it
-  // when the chunk starts at a keep-last coarse plane (then the fine plane
-  // pidx(qz0) - 2 and its interpolation planes are needed)
-  int t_start = qz0 > 0 ? qz0 - 1 : 0;
-  if (qz0 >= 2 && pidx(qz0, nz) - pidx(qz0 - 1, nz) == 1) t_start = qz0 - 2;
-  const int t_end = min(qz1, mz - 1);
-
-  const TI* in = static_cast<const TI*>(a.in);
-  const TS* wax = a.wa[2]; const TS* wbx = a.wb[2];
-  const TS* way = a.wa[1]; const TS* wby = a.wb[1];
-  const TS* waz = a.wa[0]; const TS* wbz = a.wb[0];
-  const TS* kx = a.k[2]; const TS* ky = a.k[1]; const TS* kz = a.k[0];
-
-  auto in_off = [&](int gz, int gy, int gx) -> int64_t {
-    if (a.in_full)
-      return fmap(gz, a.s[0], a.N[0]) * a.in_sz + fmap(gy, a.s[1], a.N[1]) * a.in_sy + fmap(gx, a.s[2], a.N[2]);
-    return int64_t(gz) * a.in_sz + int64_t(gy) * a.in_sy + gx;
-  };
-  auto load_plane = [&](TI* dst, int gz) {
-    for (int e = tid; e < RE; e += NT) {
-      const int r = e / RX, c = e - r * RX;
-      cp_async(dst + r * RXP + c, in + in_off(gz, ry0 + r, rx0 + c), int(sizeof(TI)));
-    }
-  };
-  auto plane_has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
-  auto issue = [&](int t) {
-    TI* st = raw + ((t - t_start) & 1) * 2 * PLANE;
-    load_plane(st, pidx(t, nz));
-    if (plane_has_fine(t)) load_plane(st + PLANE, pidx(t, nz) - 1);
-    cp_commit();
-  };
-
-  // K_z accumulators for coarse planes t-1, t, t+1
-  const int qy = qy0 + ty, qx = qx0 + tx;
-  const bool own = (qy < qy1) && (qx < qx1);
-  TS acc0 = TS(0), acc1 = TS(0), acc2 = TS(0);
-  TS* Iprev = Ibuf;
-  TS* Inext = Ibuf + PLANE;
-
-  // x then y stencil of the plane in cb, result for (qy, qx) returned
-  auto stencil_xy = [&]() -> TS {
-    if (qx < qx1) {
-      const int p = pidx(qx, nx);
-      const TS* kr = kx + 5 * qx;
-      for (int r = ty; r < RY; r += BY) {
-        TS s = TS(0);
-#pragma unroll
-        for (int o = -2; o <= 2; ++o) {
-          const int j = p + o;
-          if (j >= 0 && j < nx) s += kr[o + 2] * cb[r * RXP + (j - rx0)];
-        }
-        gxb[r * BX + tx] = s;
-      }
-    }
-    __syncthreads();
-    TS g = TS(0);
-    if (own) {
-      const int p = pidx(qy, ny);
-      const TS* kr = ky + 5 * qy;
-#pragma unroll
-      for (int o = -2; o <= 2; ++o) {
-        const int j = p + o;
-        if (j >= 0 && j < ny) g += kr[o + 2] * gxb[(j - ry0) * BX + tx];
-      }
-    }
-    return g;
-  };
-  auto accumulate_z = [&](int t, int gz, TS g) {
-    // contributions of fine plane gz to coarse planes t-1, t, t+1
-#pragma unroll
-    for (int d = -1; d <= 1; ++d) {
-      const int q = t + d;
-      if (q < qz0 || q >= qz1) continue;
-      const int off = gz - pidx(q, nz);
-      if (off < -2 || off > 2) continue;
-      const TS wgt = kz[5 * q + off + 2];
-      if (d == -1) acc0 += wgt * g;
-      else if (d == 0) acc1 += wgt * g;
-      else acc2 += wgt * g;
-    }
-  };
-  auto store_y = [&](int gz, const TI* vplane, bool zc) {
-    if (MODE != MODE_DEC || !a.write_y) return;
-    TD* y = static_cast<TD*>(a.y);
-    const int64_t zoff = fmap(gz, a.s[0], a.N[0]) * a.y_sz;
-    for (int e = tid; e < RE; e += NT) {
-      const int r = e / RX, c = e - r * RX;
-      const int gy = ry0 + r, gx = rx0 + c;
-      if (gy < oy0 || gy >= oy1 || gx < ox0 || gx >= ox1) continue;
-      const bool allc = zc && is_coarse(gy, ny) && is_coarse(gx, nx);
-      // all-coarse nodes get their (uncorrected) value as a placeholder that a
-      // coarser level overwrites; it keeps the row's sectors fully written.
-      const TS v = allc ? TS(vplane[r * RXP + c]) : cb[r * RXP + c];
-      y[zoff + fmap(gy, a.s[1], a.N[1]) * a.y_sy + fmap(gx, a.s[2], a.N[2])] = TD(v);
-    }
-  };
-
-  issue(t_start);
-  for (int t = t_start; t <= t_end; ++t) {
-    if (t < t_end) {
-      issue(t + 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const TI* vc = raw + ((t - t_start) & 1) * 2 * PLANE;
-    const TI* vf = vc + PLANE;
-    const int Pc = pidx(t, nz);
-    const bool has_f = plane_has_fine(t);
-    const bool owned_c = (t >= qz0) && (t < qz1);
-    // ---- coarse-in-z plane Pc: xy interpolant and coefficients
-    for (int e = tid; e < RE; e += NT) {
-      const int r = e / RX, c = e - r * RX;
-      const int gy = ry0 + r, gx = rx0 + c;
-      const bool yc = is_coarse(gy, ny), xc = is_coarse(gx, nx);
-      if (MODE == MODE_DEC) {
-        const TS v = TS(vc[r * RXP + c]);
-        TS I;
-        if (yc && xc) {
-          I = v;
-        } else if (yc) {
-          I = wax[gx] * TS(vc[r * RXP + c - 1]) + wbx[gx] * TS(vc[r * RXP + c + 1]);
-        } else if (xc) {
-          I = way[gy] * TS(vc[(r - 1) * RXP + c]) + wby[gy] * TS(vc[(r + 1) * RXP + c]);
-        } else {
-          const TS lo = wax[gx] * TS(vc[(r - 1) * RXP + c - 1]) + wbx[gx] * TS(vc[(r - 1) * RXP + c + 1]);
-          const TS hi = wax[gx] * TS(vc[(r + 1) * RXP + c - 1]) + wbx[gx] * TS(vc[(r + 1) * RXP + c + 1]);
-          I = way[gy] * lo + wby[gy] * hi;
-        }
-        Inext[r * RXP + c] = I;
-        cb[r * RXP + c] = v - I;
-      } else {
-        cb[r * RXP + c] = (yc && xc) ? TS(0) : TS(vc[r * RXP + c]);
-      }
-    }
-    __syncthreads();
-    if (owned_c) store_y(Pc, vc, true);
-    {
-      const TS g = stencil_xy();
-      accumulate_z(t, Pc, g);
-    }
-    if (MODE == MODE_DEC && owned_c && own) {
-      const int gy = pidx(qy, ny), gx = pidx(qx, nx);
-      a.w[int64_t(t) * a.c_sz + int64_t(qy) * a.c_sy + qx] = TW(vc[(gy - ry0) * RXP + (gx - rx0)]);
-    }
-    __syncthreads();
-    // ---- fine-in-z plane Pc-1
-    if (has_f) {
-      const int Pf = Pc - 1;
-      const bool owned_f = (t > qz0) && (t <= qz1);
-      if (MODE == MODE_DEC) {
-        const TS za = waz[Pf], zb = wbz[Pf];
-        for (int e = tid; e < RE; e += NT) {
-          const int r = e / RX, c = e - r * RX;
-          cb[r * RXP + c] = TS(vf[r * RXP + c]) - (za * Iprev[r * RXP + c] + zb * Inext[r * RXP + c]);
-        }
-      } else {
-        for (int e = tid; e < RE; e += NT) {
-          const int r = e / RX, c = e - r * RX;
-          cb[r * RXP + c] = TS(vf[r * RXP + c]);
-        }
-      }
-      __syncthreads();
-      if (owned_f) store_y(Pf, vf, false);
-      const TS g = stencil_xy();
-      accumulate_z(t, Pf, g);
-      __syncthreads();
-    }
-    // coarse plane t-1 is complete
-    if (own && t - 1 >= qz0 && t - 1 < qz1) a.f[int64_t(t - 1) * a.c_sz + int64_t(qy) * a.c_sy + qx] = TW(acc0);
-    acc0 = acc1;
-    acc1 = acc2;
-    acc2 = TS(0);
-    TS* tmp = Iprev;
-    Iprev = Inext;
-    Inext = tmp;
-  }
-  if (own && t_end == mz - 1 && qz1 == mz) a.f[int64_t(mz - 1) * a.c_sz + int64_t(qy) * a.c_sy + qx] = TW(acc0);
-}
-
-template <typename TI, typename TS>
-constexpr size_t load_smem_bytes() {
-  return sizeof(TI) * 4 * PLANE + sizeof(TS) * (3 * PLANE + RYMAX * BX);
-}
+#include "mgr_level.cuh"
 
 // ---------------------------------------------------------------------------
 // In-place decomposition of the finest level: coefficients written pointwise
@@ -452,51 +216,6 @@ __global__ void k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline
   }
 }
 
-// ---------------------------------------------------------------------------
-// Recompose: v = c + (P_z x P_y x P_x) v_coarse at every level-l node
-// ---------------------------------------------------------------------------
-template <typename TD, typename TO, typename TS, typename TW>
-__global__ void k_interp(const TD* __restrict__ y, int64_t y_sz, int64_t y_sy, int3 n, longlong3 s, longlong3 N,
-                         const TW* __restrict__ w, int64_t c_sz, int64_t c_sy, TO* __restrict__ out, int64_t o_sz,
-                         int64_t o_sy, const TS* waz, const TS* wbz, const TS* way, const TS* wby, const TS* wax,
-                         const TS* wbx) {
-  const int64_t total = int64_t(n.x) * n.y * n.z;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
-    const int gx = int(e % n.z);
-    const int64_t rest = e / n.z;
-    const int gy = int(rest % n.y), gz = int(rest / n.y);
-    int qz[2], qy[2], qx[2];
-    TS wz[2], wy[2], wx[2];
-    int cz, cy, cx;
-    auto axis = [&](int g, int nn, const TS* wa, const TS* wb, int* q, TS* wt, int& cnt) {
-      if (is_coarse(g, nn)) {
-        q[0] = cidx(g); wt[0] = TS(1); cnt = 1;
-      } else {
-        q[0] = cidx(g - 1); wt[0] = wa[g];
-        q[1] = cidx(g + 1); wt[1] = wb[g];
-        cnt = 2;
-      }
-    };
-    axis(gz, n.x, waz, wbz, qz, wz, cz);
-    axis(gy, n.y, way, wby, qy, wy, cy);
-    axis(gx, n.z, wax, wbx, qx, wx, cx);
-    TS I = TS(0);
-    for (int a = 0; a < cz; ++a) {
-      TS Iy = TS(0);
-      for (int b = 0; b < cy; ++b) {
-        const TW* row = w + int64_t(qz[a]) * c_sz + int64_t(qy[b]) * c_sy;
-        TS Ix = (cx == 1) ? TS(row[qx[0]]) : wx[0] * TS(row[qx[0]]) + wx[1] * TS(row[qx[1]]);
-        Iy = (cy == 1) ? Ix : (b == 0 ? wy[0] * Ix : Iy + wy[1] * Ix);
-      }
-      I = (cz == 1) ? Iy : (a == 0 ? wz[0] * Iy : I + wz[1] * Iy);
-    }
-    const bool allc = (cz == 1) && (cy == 1) && (cx == 1);
-    TS c = TS(0);
-    if (!allc) c = TS(y[fmap(gz, s.x, N.x) * y_sz + fmap(gy, s.y, N.y) * y_sy + fmap(gx, s.z, N.z)]);
-    out[int64_t(gz) * o_sz + int64_t(gy) * o_sy + gx] = TO(c + I);
-  }
-}
-
 // Coarsest grid <-> nodal positions (dir 0: gather nodal -> compact; 1: scatter)
 template <typename TD, typename TW>
 __global__ void k_coarsest(TD* y, int64_t y_sz, int64_t y_sy, TW* w, int3 n, longlong3 s, longlong3 N, int dir) {
@@ -539,10 +258,26 @@ inline Bufs split_ws(const mgr_plan* p, void* ws) {
   return Bufs{b, b + p->ws_a, b + p->ws_a + p->ws_b};
 }
 
+// Tile configuration of the level pass per stencil type: 8 warps with two
+// row pairs each (two CTAs per SM); FP64 uses a single cp.async stage (the
+// FP64 pipe, not memory latency, bounds it, and the smaller footprint keeps
+// two CTAs per SM), FP32 two stages.
+template <typename TS>
+struct LevelCfg;
+template <>
+struct LevelCfg<double> {
+  static constexpr int NW = 8, RPW = 2, STAGES = 1;
+};
+template <>
+struct LevelCfg<float> {
+  static constexpr int NW = 8, RPW = 2, STAGES = 2;
+};
+constexpr int kInterpNW = 8, kInterpRPW = 2;
+
 template <typename TS, typename TW>
-LoadArgs<TS, TW> load_args(const mgr_plan* p, int l) {
+LevelArgs<TS, TW> level_args(const mgr_plan* p, int l) {
   const LevelGeom& g = p->geom[l];
-  LoadArgs<TS, TW> a{};
+  LevelArgs<TS, TW> a{};
   const TS* T = table<TS>(p);
   for (int k = 0; k < 3; ++k) {
     a.n[k] = g.ax[k].n;
@@ -560,16 +295,80 @@ LoadArgs<TS, TW> load_args(const mgr_plan* p, int l) {
   return a;
 }
 
+// Number of z chunks for `tiles` xy tiles and mz coarse planes: minimise
+// waves x planes streamed per CTA (each chunk also streams ~1.5 halo planes).
+inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_sm) {
+  const int64_t slots = int64_t(p->ctx->num_sms) * ctas_per_sm;
+  int best = 1;
+  double best_cost = 1e300;
+  const int cmax = std::max(1, std::min(mz, 64));
+  for (int c = 1; c <= cmax; ++c) {
+    const int len = (mz + c - 1) / c;
+    if (c > 1 && len < 4) break;
+    const int cc = (mz + len - 1) / len;
+    const int64_t waves = (tiles * cc + slots - 1) / slots;
+    const double cost = double(waves) * (len + 1.5);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
 template <typename TS, typename TW>
-dim3 load_grid(const mgr_plan* p, LoadArgs<TS, TW>& a) {
-  const int gx = (a.m[2] + BX - 1) / BX, gy = (a.m[1] + BY - 1) / BY;
-  // enough CTAs for ~2 waves at 2 CTAs/SM; each chunk streams >= 4 coarse planes
-  const int64_t want = int64_t(p->ctx->num_sms) * 4;
-  int chunks = int(std::max<int64_t>(1, want / std::max(1, gx * gy)));
-  chunks = std::min(chunks, std::max(1, a.m[0] / 4));
+dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
+  using C = LevelCfg<TS>;
+  using G = LevelTile<C::NW, C::RPW>;
+  const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
+  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   return dim3(gx, gy, gz);
+}
+
+template <int MODE, typename TI, typename TD, typename TS, typename TW>
+void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
+  using C = LevelCfg<TS>;
+  constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
+  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  dim3 grid = level_grid(p, a);
+  kern<<<grid, C::NW * 32, sm, st>>>(a);
+}
+
+template <typename TD, typename TO, typename TS, typename TW>
+void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st) {
+  const LevelGeom& g = p->geom[l];
+  const TS* T = table<TS>(p);
+  InterpArgs<TS, TW> a{};
+  for (int k = 0; k < 3; ++k) {
+    a.n[k] = g.ax[k].n;
+    a.m[k] = g.ax[k].m;
+    a.s[k] = g.ax[k].s;
+    a.N[k] = g.ax[k].N;
+    a.wa[k] = T + g.ax[k].o_wa;
+    a.wb[k] = T + g.ax[k].o_wb;
+  }
+  a.c = c;
+  a.y_sz = p->full[1] * p->full[2];
+  a.y_sy = p->full[2];
+  a.w = w;
+  a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
+  a.c_sy = g.ax[2].m;
+  a.out = out;
+  a.out_full = out_full;
+  a.o_sz = out_full ? a.y_sz : int64_t(g.ax[1].n) * g.ax[2].n;
+  a.o_sy = out_full ? a.y_sy : int64_t(g.ax[2].n);
+  constexpr int BY = kInterpNW * kInterpRPW;
+  const int gx = (a.m[2] + 31) / 32, gy = (a.m[1] + BY - 1) / BY;
+  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
+  a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
+  const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
+  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
 }
 
 template <typename TW>
@@ -660,32 +459,25 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   TW* cur = nullptr;  // compact level-l values for l < L
   for (int l = L; l >= 1; --l) {
     TW* nxt = static_cast<TW*>(((L - l) % 2 == 0) ? b.A : b.B);
-    auto a = load_args<TS, TW>(p, l);
+    auto a = level_args<TS, TW>(p, l);
     a.y = out;
     a.w = nxt;
     a.f = F;
     a.write_y = (l == L && inplace) ? 0 : 1;
-    dim3 grid = load_grid(p, a);
-    dim3 block(BX, BY);
+    rec_begin(st);
     if (l == L) {
       a.in = in;
       a.in_full = 1;
       a.in_sz = a.y_sz;
       a.in_sy = a.y_sy;
-      constexpr size_t sm = load_smem_bytes<TD, TS>();
-      cudaFuncSetAttribute(k_level_load<MODE_DEC, TD, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      rec_begin(st);
-      k_level_load<MODE_DEC, TD, TD, TS, TW><<<grid, block, sm, st>>>(a);
+      launch_level<0, TD, TD, TS, TW>(p, a, st);
     } else {
       const LevelGeom& g = p->geom[l];
       a.in = cur;
       a.in_full = 0;
       a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
       a.in_sy = g.ax[2].n;
-      constexpr size_t sm = load_smem_bytes<TW, TS>();
-      cudaFuncSetAttribute(k_level_load<MODE_DEC, TW, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      rec_begin(st);
-      k_level_load<MODE_DEC, TW, TD, TS, TW><<<grid, block, sm, st>>>(a);
+      launch_level<0, TW, TD, TS, TW>(p, a, st);
     }
     cudaError_t e = cudaGetLastError();
     {
@@ -751,7 +543,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if (e != cudaSuccess) return e;
   }
   for (int l = 1; l <= L; ++l) {
-    auto a = load_args<TS, TW>(p, l);
+    auto a = level_args<TS, TW>(p, l);
     a.in = in;
     a.in_full = 1;
     a.in_sz = a.y_sz;
@@ -760,12 +552,8 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     a.w = nullptr;
     a.y = nullptr;
     a.write_y = 0;
-    dim3 grid = load_grid(p, a);
-    dim3 block(BX, BY);
-    constexpr size_t sm = load_smem_bytes<TD, TS>();
-    cudaFuncSetAttribute(k_level_load<MODE_REC, TD, TD, TS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     rec_begin(st);
-    k_level_load<MODE_REC, TD, TD, TS, TW><<<grid, block, sm, st>>>(a);
+    launch_level<1, TD, TD, TS, TW>(p, a, st);
     cudaError_t e = cudaGetLastError();
     {
       const Work wk = work_level_load(p, l, false);
@@ -773,23 +561,12 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     }
     if (e != cudaSuccess) return e;
     if ((e = solve_level<TW>(p, l, F, cur, SOLVE_SUB, st)) != cudaSuccess) return e;
-    const LevelGeom& g = p->geom[l];
-    const TS* T = table<TS>(p);
-    const int3 n = make_int3(g.ax[0].n, g.ax[1].n, g.ax[2].n);
-    const longlong3 s = make_longlong3(g.ax[0].s, g.ax[1].s, g.ax[2].s);
-    const longlong3 N = make_longlong3(g.ax[0].N, g.ax[1].N, g.ax[2].N);
-    const int64_t total = g.fine_count();
-    const int64_t c_sz = int64_t(g.ax[1].m) * g.ax[2].m, c_sy = g.ax[2].m;
     rec_begin(st);
     if (l == L) {
-      k_interp<TD, TD, TS, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(
-          static_cast<const TD*>(in), a.y_sz, a.y_sy, n, s, N, cur, c_sz, c_sy, static_cast<TD*>(out), a.y_sz, a.y_sy,
-          T + g.ax[0].o_wa, T + g.ax[0].o_wb, T + g.ax[1].o_wa, T + g.ax[1].o_wb, T + g.ax[2].o_wa, T + g.ax[2].o_wb);
+      launch_interp<TD, TD, TS, TW>(p, l, in, cur, out, 1, st);
     } else {
       TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
-      k_interp<TD, TW, TS, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(
-          static_cast<const TD*>(in), a.y_sz, a.y_sy, n, s, N, cur, c_sz, c_sy, nxt, int64_t(n.y) * n.z, n.z,
-          T + g.ax[0].o_wa, T + g.ax[0].o_wb, T + g.ax[1].o_wa, T + g.ax[1].o_wb, T + g.ax[2].o_wa, T + g.ax[2].o_wb);
+      launch_interp<TD, TW, TS, TW>(p, l, in, cur, nxt, 0, st);
       cur = nxt;
     }
     e = cudaGetLastError();

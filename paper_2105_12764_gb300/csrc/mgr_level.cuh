@@ -1,0 +1,646 @@
+// mgr_level.cuh -- the level pass of decomposition (coefficients + load
+// vector) and the load-vector pass of recomposition, for sm_103a.
+//
+// Per level l (level grid n -> coarse grid m), a CTA owns BX x BY coarse
+// (y, x) nodes and a chunk of coarse z planes.  It streams the fine z planes
+// of its region (the owned fine nodes plus the two-node halo the 5-tap
+// mass-transfer stencil needs) in pairs: the coarse-in-z plane p(t) and the
+// fine-in-z plane p(t)-1 between p(t-1) and p(t).
+//
+// Thread mapping (fixed for the CTA's lifetime, so every per-row and
+// per-column weight and address is computed once): lane l owns the fine
+// column pair (rx0 + 2l, rx0 + 2l + 1) of the region, warp w owns RPW fine
+// row pairs.  The region starts on a coarse node, so the first node of every
+// pair is coarse and the second is the fine node between two coarse ones
+// (or, at the end of an axis whose length is even, the last coarse node).
+//
+// Coefficients (Sec. II.A.1), separable and in the paper's FMA form
+// (Table "fma"): on a coarse-z plane the x interpolant of a coarse row uses
+// the right neighbour's value (warp shuffle), the y interpolant of a fine row
+// uses the next coarse row's interpolant (the next pair of the same thread,
+// or the next warp's first pair through shared memory); a fine-z plane
+// interpolates between the xy interpolants of its two coarse planes, which
+// each thread keeps in registers.
+//
+// Load vector f' = (x_k D_k^-1 K_k) c (Sec. II.A.2, III.A.2): c goes to
+// shared memory, the x stencil runs on rows (5 taps; 2 on rows that are
+// coarse in y and z, where c vanishes on coarse nodes), the y stencil on
+// the x results, and the z stencil accumulates in registers over the
+// streamed planes.  Four barriers per plane pair.
+#pragma once
+
+template <int NW, int RPW>
+struct LevelTile {
+  static constexpr int NT = NW * 32;
+  static constexpr int BX = 30;            // coarse x outputs per CTA
+  static constexpr int BY = NW * RPW - 2;  // coarse y outputs per CTA
+  static constexpr int RC = 64;            // fine column slots (region width <= 2*BX+3 = 63)
+  static constexpr int RR = 2 * NW * RPW;  // fine row slots (region height <= 2*BY+3 = RR-1)
+  static constexpr int CP = RC + 2;        // c row pitch: even, so column pairs stay 8/16-byte aligned
+};
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <typename TS, typename TW>
+struct LevelArgs {
+  const void* in;  // DEC: level-l values; REC: nodal coefficients (full grid)
+  int64_t in_sz, in_sy;
+  int in_full;     // 1: `in` is addressed through the full-grid map min(i*s, N-1)
+  void* y;         // DEC: nodal output (full grid)
+  int64_t y_sz, y_sy;
+  TW* w;           // DEC: coarse nodal values (compact m grid)
+  TW* f;           // load vector (compact m grid)
+  int64_t c_sz, c_sy;
+  int n[3], m[3];
+  int64_t s[3], N[3];
+  const TS* wa[3];
+  const TS* wb[3];
+  const TS* k[3];
+  int qz_chunk;
+  int write_y;
+};
+
+template <int NW, int RPW, int STAGES, typename TI, typename TS>
+constexpr size_t level_smem_bytes() {
+  using G = LevelTile<NW, RPW>;
+  return sizeof(TI) * STAGES * 2 * G::RR * G::RC +
+         sizeof(TS) * (2 * G::RR * G::CP + NW * G::RC + 2 * G::RR * 32);
+}
+
+// Copy the element pair (c0, c0+1) of one row into shared memory: one
+// 2-element cp.async when both are in the region, adjacent in memory and
+// aligned (uniform across a warp: every lane of a row has the same parity),
+// else one copy per element.
+template <typename T>
+__device__ __forceinline__ void load_pair(T* dst, const T* src0, const T* src1, bool v0, bool v1, bool contig) {
+  if (v0 && v1 && contig && ((reinterpret_cast<uintptr_t>(src0) & (2 * sizeof(T) - 1)) == 0)) {
+    cp_async(dst, src0, int(2 * sizeof(T)));
+  } else {
+    if (v0) cp_async(dst, src0, int(sizeof(T)));
+    if (v1) cp_async(dst + 1, src1, int(sizeof(T)));
+  }
+}
+
+// Store a pair of output values (to adjacent or separate addresses).
+template <typename T>
+__device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bool w1, bool contig) {
+  if (w0 && w1 && contig && ((reinterpret_cast<uintptr_t>(p0) & (2 * sizeof(T) - 1)) == 0)) {
+    typename Pair<T>::type v;
+    v.x = a0;
+    v.y = a1;
+    *reinterpret_cast<typename Pair<T>::type*>(p0) = v;
+  } else {
+    if (w0) *p0 = a0;
+    if (w1) *p1 = a1;
+  }
+}
+
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
+  using G = LevelTile<NW, RPW>;
+  using TS2 = typename Pair<TS>::type;
+  using TI2 = typename Pair<TI>::type;
+  constexpr int RR = G::RR, RC = G::RC, CP = G::CP;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TI* stage = reinterpret_cast<TI*>(smem_raw);                                       // [STAGES][2][RR][RC]
+  TS* cbuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * STAGES * 2 * RR * RC);  // [2][RR][CP]
+  TS* xch = cbuf + 2 * RR * CP;                                                     // [NW][RC]
+  TS* gxb = xch + NW * RC;                                                          // [2][RR][32]
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
+  const int mz = a.m[0], my = a.m[1], mx = a.m[2];
+  const int qx0 = blockIdx.x * G::BX, qx1 = min(qx0 + G::BX, mx);
+  const int qy0 = blockIdx.y * G::BY, qy1 = min(qy0 + G::BY, my);
+  const int qz0 = blockIdx.z * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
+  const int rx0 = max(region_start(qx0, nx), 0), rx1 = min(pidx(qx1 - 1, nx) + 2, nx - 1);
+  const int ry0 = max(region_start(qy0, ny), 0), ry1 = min(pidx(qy1 - 1, ny) + 2, ny - 1);
+  const int ox0 = pidx(qx0, nx), ox1 = (qx1 == mx) ? nx : pidx(qx1, nx);
+  const int oy0 = pidx(qy0, ny), oy1 = (qy1 == my) ? ny : pidx(qy1, ny);
+  int t_start = qz0 > 0 ? qz0 - 1 : 0;
+  if (qz0 >= 2 && pidx(qz0, nz) - pidx(qz0 - 1, nz) == 1) t_start = qz0 - 2;
+  const int t_end = min(qz1, mz - 1);
+
+  const TI* __restrict__ in = static_cast<const TI*>(a.in);
+  TD* __restrict__ yout = static_cast<TD*>(a.y);
+  const bool wy = (MODE == 0) && a.write_y;
+
+  // ---- per-lane column constants (in-plane offsets fit in 32 bits)
+  const int cx0 = 2 * lane;
+  const int gx0 = rx0 + cx0, gx1 = gx0 + 1;
+  const bool vx0 = gx0 <= rx1, vx1 = gx1 <= rx1;
+  const bool fx1 = vx1 && gx1 < nx - 1;  // gx1 is odd: fine unless it is the last node
+  const TS wax1 = fx1 ? a.wa[2][gx1] : TS(0), wbx1 = fx1 ? a.wb[2][gx1] : TS(0);
+  const bool owx0 = vx0 && gx0 >= ox0 && gx0 < ox1, owx1 = vx1 && gx1 >= ox0 && gx1 < ox1;
+  const int ic0 = a.in_full ? int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])) : gx0;
+  const int ic1 = a.in_full ? int(fmap(min(gx1, nx - 1), a.s[2], a.N[2])) : gx1;
+  const bool icontig = ic1 == ic0 + 1;
+  const int yc0 = int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])), yc1 = int(fmap(min(gx1, nx - 1), a.s[2], a.N[2]));
+  const bool ycontig = yc1 == yc0 + 1;
+
+  // ---- x stencil of this lane's output column
+  const int nbx = qx1 - qx0;
+  const bool kxo = lane < nbx;
+  const int qxo = min(qx0 + lane, mx - 1);
+  const int px = pidx(qxo, nx);
+  const int dx = px - rx0;  // slot of the stencil centre
+  TS kx[5];
+  unsigned kxm = 0;  // taps inside the grid
+#pragma unroll
+  for (int o = 0; o < 5; ++o) {
+    kx[o] = a.k[2][5 * qxo + o];
+    const int j = px + o - 2;
+    if (j >= 0 && j < nx) kxm |= 1u << o;
+  }
+  // interior column: taps px +- 1 fine, px and px +- 2 coarse, even slot
+  const bool kx_generic = kxm == 31u && (px & 1) == 0 && px + 1 < nx - 1;
+
+  // ---- per-row constants (RPW row pairs per warp)
+  int gy0[RPW];
+  bool vy0[RPW], vy1[RPW], fy1[RPW], owy0[RPW], owy1[RPW];
+  TS way1[RPW], wby1[RPW];
+  int ir0[RPW], ir1[RPW], yr0[RPW], yr1[RPW];
+  // y stencil of this thread's output rows
+  const int nby = qy1 - qy0;
+  TS ky[RPW][5];
+  unsigned kym[RPW];
+  int dyo[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    gy0[k] = ry0 + 2 * (warp * RPW + k);
+    const int g1 = gy0[k] + 1;
+    vy0[k] = gy0[k] <= ry1;
+    vy1[k] = g1 <= ry1;
+    fy1[k] = vy1[k] && g1 < ny - 1;
+    way1[k] = fy1[k] ? a.wa[1][g1] : TS(0);
+    wby1[k] = fy1[k] ? a.wb[1][g1] : TS(0);
+    owy0[k] = vy0[k] && gy0[k] >= oy0 && gy0[k] < oy1;
+    owy1[k] = vy1[k] && g1 >= oy0 && g1 < oy1;
+    const int c0 = min(gy0[k], ny - 1), c1 = min(g1, ny - 1);
+    ir0[k] = int(a.in_full ? fmap(c0, a.s[1], a.N[1]) * a.in_sy : int64_t(c0) * a.in_sy);
+    ir1[k] = int(a.in_full ? fmap(c1, a.s[1], a.N[1]) * a.in_sy : int64_t(c1) * a.in_sy);
+    yr0[k] = int(fmap(c0, a.s[1], a.N[1]) * a.y_sy);
+    yr1[k] = int(fmap(c1, a.s[1], a.N[1]) * a.y_sy);
+    const int qy = min(qy0 + warp * RPW + k, my - 1);
+    const int py = pidx(qy, ny);
+    dyo[k] = py - ry0;
+    kym[k] = 0;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      ky[k][o] = a.k[1][5 * qy + o];
+      const int jj = py + o - 2;
+      if (jj >= 0 && jj < ny) kym[k] |= 1u << o;
+    }
+  }
+
+  auto iplane = [&](int g) -> int64_t {
+    return a.in_full ? fmap(g, a.s[0], a.N[0]) * a.in_sz : int64_t(g) * a.in_sz;
+  };
+  auto load_plane = [&](TI* sb, int gz) {
+    const TI* base = in + iplane(gz);
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int r0 = 2 * (warp * RPW + k);
+      if (vy0[k]) load_pair(sb + r0 * RC + cx0, base + ir0[k] + ic0, base + ir0[k] + ic1, vx0, vx1, icontig);
+      if (vy1[k]) load_pair(sb + (r0 + 1) * RC + cx0, base + ir1[k] + ic0, base + ir1[k] + ic1, vx0, vx1, icontig);
+    }
+  };
+  auto has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
+  auto issue = [&](int t) {
+    TI* sb = stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0);
+    load_plane(sb, pidx(t, nz));
+    if (has_fine(t)) load_plane(sb + RR * RC, pidx(t, nz) - 1);
+    cp_commit();
+  };
+
+  TS Ip[RPW][4], In[RPW][4];
+  TS acc0[RPW], acc1[RPW], acc2[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    acc0[k] = acc1[k] = acc2[k] = TS(0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Ip[k][e] = In[k][e] = TS(0);
+  }
+
+  issue(t_start);
+  for (int t = t_start; t <= t_end; ++t) {
+    if (STAGES == 2) {
+      if (t < t_end) {
+        issue(t + 1);
+        cp_wait<1>();
+      } else {
+        cp_wait<0>();
+      }
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const TI* sc = stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0);
+    const TI* sf = sc + RR * RC;
+    const int Pc = pidx(t, nz);
+    const bool hf = has_fine(t);
+    const int Pf = Pc - 1;
+    const bool own_c = (t >= qz0) && (t < qz1);
+    const bool own_f = hf && (t > qz0) && (t <= qz1);
+
+    // ---- this thread's values of both planes (pairs from shared memory)
+    TS vc[RPW][4], vf[RPW][4];
+    TI rc[RPW][4];  // raw coarse-plane values: exact copies for the coarse workspace
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int r0 = 2 * (warp * RPW + k);
+      const TI2 p0 = *reinterpret_cast<const TI2*>(sc + r0 * RC + cx0);
+      const TI2 p1 = *reinterpret_cast<const TI2*>(sc + (r0 + 1) * RC + cx0);
+      rc[k][0] = p0.x;
+      rc[k][1] = p0.y;
+      rc[k][2] = p1.x;
+      rc[k][3] = p1.y;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) vc[k][e] = TS(rc[k][e]);
+      if (hf) {
+        const TI2 f0 = *reinterpret_cast<const TI2*>(sf + r0 * RC + cx0);
+        const TI2 f1 = *reinterpret_cast<const TI2*>(sf + (r0 + 1) * RC + cx0);
+        vf[k][0] = TS(f0.x);
+        vf[k][1] = TS(f0.y);
+        vf[k][2] = TS(f1.x);
+        vf[k][3] = TS(f1.y);
+      } else {
+        vf[k][0] = vf[k][1] = vf[k][2] = vf[k][3] = TS(0);
+      }
+    }
+    // ---- coarse-z plane: x interpolants of the coarse rows
+    TS v12[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const TS v02 = __shfl_down_sync(FULL, vc[k][0], 1);
+      v12[k] = __shfl_down_sync(FULL, vc[k][2], 1);
+      if (MODE == 0) {
+        In[k][0] = vc[k][0];
+        In[k][1] = fx1 ? wax1 * vc[k][0] + wbx1 * v02 : vc[k][1];
+      }
+    }
+    if (MODE == 0) *reinterpret_cast<TS2*>(xch + warp * RC + cx0) = TS2{In[0][0], In[0][1]};
+    __syncthreads();
+    if (STAGES == 1 && t < t_end) issue(t + 1);  // every thread has read the stage buffer
+
+    // ---- coefficients of both planes -> shared memory and the nodal output
+    TS* cc = cbuf;
+    TS* cf = cbuf + RR * CP;
+    TD* yzc = yout + fmap(Pc, a.s[0], a.N[0]) * a.y_sz;
+    TD* yzf = yout + fmap(max(Pf, 0), a.s[0], a.N[0]) * a.y_sz;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int r0 = 2 * (warp * RPW + k);
+      TS c[4];
+      if (MODE == 0) {
+        TS n0, n1;
+        if (k + 1 < RPW) {
+          n0 = In[k + 1 < RPW ? k + 1 : k][0];
+          n1 = In[k + 1 < RPW ? k + 1 : k][1];
+        } else if (warp + 1 < NW) {
+          const TS2 nx2 = *reinterpret_cast<const TS2*>(xch + (warp + 1) * RC + cx0);
+          n0 = nx2.x;
+          n1 = nx2.y;
+        } else {
+          n0 = n1 = TS(0);
+        }
+        if (fy1[k]) {
+          In[k][2] = way1[k] * In[k][0] + wby1[k] * n0;
+          In[k][3] = way1[k] * In[k][1] + wby1[k] * n1;
+        } else {
+          In[k][2] = vc[k][2];
+          In[k][3] = fx1 ? wax1 * vc[k][2] + wbx1 * v12[k] : vc[k][3];
+        }
+        c[0] = TS(0);
+        c[1] = vc[k][1] - In[k][1];
+        c[2] = vc[k][2] - In[k][2];
+        c[3] = vc[k][3] - In[k][3];
+      } else {
+        c[0] = TS(0);
+        c[1] = fx1 ? vc[k][1] : TS(0);
+        c[2] = fy1[k] ? vc[k][2] : TS(0);
+        c[3] = (fx1 || fy1[k]) ? vc[k][3] : TS(0);
+      }
+      *reinterpret_cast<TS2*>(cc + r0 * CP + cx0) = TS2{c[0], c[1]};
+      *reinterpret_cast<TS2*>(cc + (r0 + 1) * CP + cx0) = TS2{c[2], c[3]};
+      if (wy && own_c) {
+        // all-coarse nodes get their (uncorrected) value as a placeholder that a
+        // coarser level overwrites; it keeps the row's sectors fully written
+        store_pair<TD>(yzc + yr0[k] + yc0, yzc + yr0[k] + yc1, TD(vc[k][0]), TD(fx1 ? c[1] : vc[k][1]),
+                       owy0[k] && owx0, owy0[k] && owx1, ycontig);
+        store_pair<TD>(yzc + yr1[k] + yc0, yzc + yr1[k] + yc1, TD(fy1[k] ? c[2] : vc[k][2]),
+                       TD((fx1 || fy1[k]) ? c[3] : vc[k][3]), owy1[k] && owx0, owy1[k] && owx1, ycontig);
+      }
+      if (MODE == 0 && own_c) {
+        // coarse nodal values of the owned all-coarse nodes
+        TW* wz = a.w + int64_t(t) * a.c_sz;
+        if (owy0[k] && owx0) wz[int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx0)] = TW(rc[k][0]);
+        if (owy0[k] && owx1 && !fx1) wz[int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx1)] = TW(rc[k][1]);
+        if (owy1[k] && !fy1[k]) {
+          if (owx0) wz[int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx0)] = TW(rc[k][2]);
+          if (owx1 && !fx1) wz[int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx1)] = TW(rc[k][3]);
+        }
+      }
+      if (hf) {
+        TS d[4];
+        if (MODE == 0) {
+          const TS za = a.wa[0][Pf], zb = a.wb[0][Pf];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) d[e] = vf[k][e] - za * Ip[k][e] - zb * In[k][e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) d[e] = vf[k][e];
+        }
+        *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
+        *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
+        if (wy && own_f) {
+          store_pair<TD>(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, TD(d[0]), TD(d[1]), owy0[k] && owx0,
+                         owy0[k] && owx1, ycontig);
+          store_pair<TD>(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, TD(d[2]), TD(d[3]), owy1[k] && owx0,
+                         owy1[k] && owx1, ycontig);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- x stencil on every row of this warp (both planes)
+    if (kxo) {
+#pragma unroll
+      for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = 2 * (warp * RPW + k) + h;
+          // rows coarse in y (of the coarse-z plane): c vanishes on coarse columns
+          const bool zero_row = h == 0 || !fy1[k];
+          TS g, gf = TS(0);
+          if (kx_generic) {
+            const TS* row = cc + r * CP + dx - 2;
+            const TS2 a01 = *reinterpret_cast<const TS2*>(row);
+            const TS2 a23 = *reinterpret_cast<const TS2*>(row + 2);
+            if (zero_row) {
+              g = kx[1] * a01.y + kx[3] * a23.y;
+            } else {
+              g = kx[0] * a01.x + kx[1] * a01.y + kx[2] * a23.x + kx[3] * a23.y + kx[4] * row[4];
+            }
+            if (hf) {
+              const TS* rf = cf + r * CP + dx - 2;
+              const TS2 b01 = *reinterpret_cast<const TS2*>(rf);
+              const TS2 b23 = *reinterpret_cast<const TS2*>(rf + 2);
+              gf = kx[0] * b01.x + kx[1] * b01.y + kx[2] * b23.x + kx[3] * b23.y + kx[4] * rf[4];
+            }
+          } else {
+            g = TS(0);
+#pragma unroll
+            for (int o = 0; o < 5; ++o)
+              if (kxm & (1u << o)) {
+                g += kx[o] * cc[r * CP + dx - 2 + o];
+                if (hf) gf += kx[o] * cf[r * CP + dx - 2 + o];
+              }
+          }
+          gxb[r * 32 + lane] = g;
+          if (hf) gxb[RR * 32 + r * 32 + lane] = gf;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- y stencil and z accumulation for this thread's outputs
+    // z weights of the two planes for coarse planes t-1, t, t+1 (uniform)
+    TS wzc[3], wzf[2];
+#pragma unroll
+    for (int dq = -1; dq <= 1; ++dq) {
+      const int q = t + dq;
+      const bool qv = q >= 0 && q < mz;
+      const int pq = qv ? pidx(q, nz) : 0;
+      const int oc = Pc - pq;
+      wzc[dq + 1] = (qv && oc >= -2 && oc <= 2) ? a.k[0][5 * q + oc + 2] : TS(0);
+      if (dq < 1) {
+        const int of = Pf - pq;
+        wzf[dq + 1] = (hf && qv && of >= -2 && of <= 2) ? a.k[0][5 * q + of + 2] : TS(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int j = warp * RPW + k;
+      if (j < nby && kxo) {
+        TS gc = TS(0), gf = TS(0);
+#pragma unroll
+        for (int o = 0; o < 5; ++o) {
+          if (kym[k] & (1u << o)) {
+            gc += ky[k][o] * gxb[(dyo[k] + o - 2) * 32 + lane];
+            if (hf) gf += ky[k][o] * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
+          }
+        }
+        acc0[k] += wzc[0] * gc;
+        acc1[k] += wzc[1] * gc;
+        acc2[k] += wzc[2] * gc;
+        if (hf) {
+          acc0[k] += wzf[0] * gf;
+          acc1[k] += wzf[1] * gf;
+        }
+        if (t - 1 >= qz0 && t - 1 < qz1)
+          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = TW(acc0[k]);
+      }
+      acc0[k] = acc1[k];
+      acc1[k] = acc2[k];
+      acc2[k] = TS(0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Ip[k][e] = In[k][e];
+    }
+  }
+  if (t_end == mz - 1 && qz1 == mz) {
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int j = warp * RPW + k;
+      if (j < nby && kxo) a.f[int64_t(mz - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = TW(acc0[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Recomposition interpolation (Sec. II.A, recomposition): level-l values
+// v = c + (P_z x P_y x P_x) v_coarse.  A CTA owns 32 x (NW*RPW) coarse
+// (x, y) nodes and a chunk of coarse z planes; lane l / warp row k own the
+// fine block {p(q), p(q)+1} x {p(q), p(q)+1} of their coarse node (the second
+// node only when a fine node lies between q and q+1).  The coarse plane tile
+// (one extra row and column for the right / lower neighbours) is staged in
+// shared memory; the xy interpolants of each coarse plane stay in registers
+// for the fine plane between it and the next one.
+// ---------------------------------------------------------------------------
+template <typename TS, typename TW>
+struct InterpArgs {
+  const void* c;  // nodal coefficients (full grid)
+  int64_t y_sz, y_sy;
+  const TW* w;    // coarse values (compact m grid)
+  int64_t c_sz, c_sy;
+  void* out;      // level-l values: full grid (out_full) or compact n grid
+  int64_t o_sz, o_sy;
+  int out_full;
+  int n[3], m[3];
+  int64_t s[3], N[3];
+  const TS* wa[3];
+  const TS* wb[3];
+  int qz_chunk;
+};
+
+template <int NW, int RPW, typename TD, typename TW>
+constexpr size_t interp_smem_bytes() {
+  return sizeof(TD) * 2 * 2 * (2 * NW * RPW) * 64 + sizeof(TW) * 2 * (NW * RPW + 1) * 33;
+}
+
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
+  constexpr int BY = NW * RPW, TR = BY + 1, TC = 33, RR = 2 * BY, RC = 64;
+  using TD2 = typename Pair<TD>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TD* stage = reinterpret_cast<TD*>(smem_raw);                                  // [2][2][RR][RC]
+  TW* tile = reinterpret_cast<TW*>(smem_raw + sizeof(TD) * 2 * 2 * RR * RC);  // [2][TR][TC]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
+  const int mz = a.m[0], my = a.m[1], mx = a.m[2];
+  const int qx0 = blockIdx.x * 32, qy0 = blockIdx.y * BY;
+  const int qz0 = blockIdx.z * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
+  const int t_end = min(qz1, mz - 1);
+  const int tcols = min(TC, mx - qx0), trows = min(TR, my - qy0);
+  const TD* __restrict__ cin = static_cast<const TD*>(a.c);
+  TO* __restrict__ out = static_cast<TO*>(a.out);
+
+  // column block of this lane: fine nodes p(qx) and, when a fine node lies
+  // between qx and qx+1, p(qx)+1
+  const int qx = qx0 + lane;
+  const bool ax = qx < mx;
+  const int gx0 = pidx(min(qx, mx - 1), nx);
+  const bool ox1 = ax && qx + 1 < mx && pidx(qx + 1, nx) - gx0 == 2;
+  const TS wax1 = ox1 ? a.wa[2][gx0 + 1] : TS(0), wbx1 = ox1 ? a.wb[2][gx0 + 1] : TS(0);
+  const int gx1 = min(gx0 + 1, nx - 1);
+  const int cc0 = int(fmap(gx0, a.s[2], a.N[2])), cc1 = int(fmap(gx1, a.s[2], a.N[2]));
+  const bool ccontig = cc1 == cc0 + 1;
+  const int oc0 = a.out_full ? cc0 : gx0, oc1 = a.out_full ? cc1 : gx1;
+  const bool ocontig = oc1 == oc0 + 1;
+  // row blocks
+  bool ay[RPW], oy1[RPW];
+  TS way1[RPW], wby1[RPW];
+  int cr0[RPW], cr1[RPW];
+  int64_t or0[RPW], or1[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int qy = qy0 + warp * RPW + k;
+    ay[k] = qy < my;
+    const int g0 = pidx(min(qy, my - 1), ny);
+    oy1[k] = ay[k] && qy + 1 < my && pidx(qy + 1, ny) - g0 == 2;
+    way1[k] = oy1[k] ? a.wa[1][g0 + 1] : TS(0);
+    wby1[k] = oy1[k] ? a.wb[1][g0 + 1] : TS(0);
+    const int g1 = min(g0 + 1, ny - 1);
+    cr0[k] = int(fmap(g0, a.s[1], a.N[1]) * a.y_sy);
+    cr1[k] = int(fmap(g1, a.s[1], a.N[1]) * a.y_sy);
+    or0[k] = (a.out_full ? fmap(g0, a.s[1], a.N[1]) : int64_t(g0)) * a.o_sy;
+    or1[k] = (a.out_full ? fmap(g1, a.s[1], a.N[1]) : int64_t(g1)) * a.o_sy;
+  }
+
+  auto has_fine = [&](int t) { return t > qz0 && pidx(t, nz) - pidx(t - 1, nz) == 2; };
+  auto load_c = [&](TD* sb, int gz) {
+    const TD* base = cin + fmap(gz, a.s[0], a.N[0]) * a.y_sz;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int r0 = 2 * (warp * RPW + k);
+      if (ay[k]) {
+        load_pair(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, ccontig);
+        if (oy1[k]) load_pair(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, ccontig);
+      }
+    }
+  };
+  auto issue = [&](int t) {
+    const int st = (t - qz0) & 1;
+    TW* tb = tile + st * TR * TC;
+    const TW* src = a.w + int64_t(t) * a.c_sz + int64_t(qy0) * a.c_sy + qx0;
+    for (int e = threadIdx.x; e < trows * TC; e += NW * 32) {
+      const int r = e / TC, cix = e - r * TC;
+      if (cix < tcols) cp_async(tb + r * TC + cix, src + int64_t(r) * a.c_sy + cix, int(sizeof(TW)));
+    }
+    TD* sb = stage + st * 2 * RR * RC;
+    if (t < qz1) load_c(sb, pidx(t, nz));
+    if (has_fine(t)) load_c(sb + RR * RC, pidx(t, nz) - 1);
+    cp_commit();
+  };
+
+  TS Ip[RPW][4], In[RPW][4];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) Ip[k][e] = In[k][e] = TS(0);
+
+  issue(qz0);
+  for (int t = qz0; t <= t_end; ++t) {
+    if (t < t_end) {
+      issue(t + 1);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const int st = (t - qz0) & 1;
+    const TW* tb = tile + st * TR * TC;
+    const TD* sc = stage + st * 2 * RR * RC;
+    const TD* sf = sc + RR * RC;
+    const int Pc = pidx(t, nz);
+    const bool own_c = t < qz1;
+    const bool hf = has_fine(t);
+    const int Pf = Pc - 1;
+    TO* ozc = out + (a.out_full ? fmap(Pc, a.s[0], a.N[0]) : int64_t(Pc)) * a.o_sz;
+    TO* ozf = out + (a.out_full ? fmap(max(Pf, 0), a.s[0], a.N[0]) : int64_t(max(Pf, 0))) * a.o_sz;
+    const TS za = hf ? a.wa[0][Pf] : TS(0), zb = hf ? a.wb[0][Pf] : TS(0);
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int r = warp * RPW + k;
+      const int r0 = 2 * r;
+      const bool act = ax && ay[k];
+      // coarse neighbours (clamped reads stay inside the staged tile)
+      const int rr1 = min(r + 1, trows - 1), cl1 = min(lane + 1, tcols - 1);
+      const int rr0 = min(r, trows - 1), cl0 = min(lane, tcols - 1);
+      const TW w00r = tb[rr0 * TC + cl0];
+      const TS w00 = TS(w00r), w01 = TS(tb[rr0 * TC + cl1]);
+      const TS w10 = TS(tb[rr1 * TC + cl0]), w11 = TS(tb[rr1 * TC + cl1]);
+      In[k][0] = w00;
+      In[k][1] = ox1 ? wax1 * w00 + wbx1 * w01 : TS(0);
+      In[k][2] = oy1[k] ? way1[k] * w00 + wby1[k] * w10 : TS(0);
+      if (ox1 && oy1[k]) {
+        const TS i21 = wax1 * w10 + wbx1 * w11;
+        In[k][3] = way1[k] * In[k][1] + wby1[k] * i21;
+      } else {
+        In[k][3] = TS(0);
+      }
+      if (act && own_c) {
+        const TD2 c0 = *reinterpret_cast<const TD2*>(sc + r0 * RC + 2 * lane);
+        store_pair<TO>(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(TS(c0.y) + In[k][1]), true, ox1, ocontig);
+        if (oy1[k]) {
+          const TD2 c1 = *reinterpret_cast<const TD2*>(sc + (r0 + 1) * RC + 2 * lane);
+          store_pair<TO>(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(TS(c1.x) + In[k][2]), TO(TS(c1.y) + In[k][3]),
+                         true, ox1, ocontig);
+        }
+      }
+      if (act && hf) {
+        const TD2 c0 = *reinterpret_cast<const TD2*>(sf + r0 * RC + 2 * lane);
+        store_pair<TO>(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
+                       TO(TS(c0.y) + za * Ip[k][1] + zb * In[k][1]), true, ox1, ocontig);
+        if (oy1[k]) {
+          const TD2 c1 = *reinterpret_cast<const TD2*>(sf + (r0 + 1) * RC + 2 * lane);
+          store_pair<TO>(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
+                         TO(TS(c1.y) + za * Ip[k][3] + zb * In[k][3]), true, ox1, ocontig);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Ip[k][e] = In[k][e];
+    }
+    __syncthreads();  // both stage buffers are reloaded two iterations later
+  }
+}

@@ -81,7 +81,10 @@ def test_3d_every_size(ctx, n):
 
 # ------------------------------------------------- multi-tile, ragged tails --
 
-MULTI = [(65, 65, 65), (70, 45, 100), (33, 130, 67), (129, 20, 9), (17, 17, 200), (2, 90, 90), (300, 70)]
+# tile edges: 30 coarse x and 14 coarse y per CTA; n = 60 (m = 31) and n = 28
+# (m = 15) put a keep-last coarse node alone in the last tile
+MULTI = [(65, 65, 65), (70, 45, 100), (33, 130, 67), (129, 20, 9), (17, 17, 200), (2, 90, 90), (300, 70),
+         (29, 28, 60), (58, 60, 121), (31, 57, 62), (12, 29, 59), (140, 30, 61)]
 
 
 @pytest.mark.parametrize("shape", MULTI)
