@@ -178,16 +178,26 @@ __global__ void __launch_bounds__(256) k_solve_strided(TW* __restrict__ f, TW* _
   }
 }
 
-// Lines along the contiguous axis: R rows of length mline staged in shared
-// memory (coalesced load/store), one thread per row for the recurrences.
+// Lines along the contiguous axis: blockDim.x rows of length mline staged in
+// shared memory with coalesced loads/stores; each thread then runs the
+// recurrences of its own row in chunks of 8 (eight independent loads, eight
+// dependent FMAs, eight stores), with the recurrence coefficients staged
+// once per CTA.
 template <typename TW, int OP>
-__global__ void k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows, int64_t row_pitch,
-                               int R, const TW* __restrict__ ta, const TW* __restrict__ tb) {
+__global__ void __launch_bounds__(128) k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows,
+                                                      int64_t row_pitch, int R, const TW* __restrict__ ta,
+                                                      const TW* __restrict__ tb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TW* s = reinterpret_cast<TW*>(smem_raw);
-  const int pitch = mline | 1;  // odd pitch spreads rows over banks
+  const int pitch = mline | 1;  // odd pitch spreads the rows of a warp over the banks
+  TW* s = reinterpret_cast<TW*>(smem_raw);  // [R][pitch]
+  TW* sa = s + R * pitch;                   // [mline]
+  TW* sb = sa + mline;                      // [mline]
   const int64_t r0 = blockIdx.x * int64_t(R);
   const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
+  for (int q = threadIdx.x; q < mline; q += blockDim.x) {
+    sa[q] = ta[q];
+    sb[q] = tb[q];
+  }
   for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
     const int r = e / mline, c = e - r * mline;
     s[r * pitch + c] = f[(r0 + r) * row_pitch + c];
@@ -195,24 +205,44 @@ __global__ void k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline
   __syncthreads();
   if (threadIdx.x < nr) {
     TW* l = s + threadIdx.x * pitch;
+    constexpr int U = 8;
     TW prev = TW(0);
-    for (int q = 0; q < mline; ++q) {
-      prev = l[q] - ta[q] * prev;
-      l[q] = prev;
+    for (int q0 = 0; q0 < mline; q0 += U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q0 + u < mline) ? l[q0 + u] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        prev = v[u] - sa[min(q0 + u, mline - 1)] * prev;
+        v[u] = prev;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q0 + u < mline) l[q0 + u] = v[u];
     }
     TW next = TW(0);
-    for (int q = mline - 1; q >= 0; --q) {
-      next = l[q] - tb[q] * next;
-      l[q] = next;
+    for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q1 - u >= 0) ? l[q1 - u] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        next = v[u] - sb[max(q1 - u, 0)] * next;
+        v[u] = next;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q1 - u >= 0) l[q1 - u] = v[u];
     }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
     const int r = e / mline, c = e - r * mline;
     const int64_t g = (r0 + r) * row_pitch + c;
-    if (OP == SOLVE_INPLACE) f[g] = s[r * pitch + c];
-    else if (OP == SOLVE_ADD) w[g] = w[g] + s[r * pitch + c];
-    else w[g] = w[g] - s[r * pitch + c];
+    const TW v = s[r * pitch + c];
+    if (OP == SOLVE_INPLACE) f[g] = v;
+    else if (OP == SOLVE_ADD) w[g] = w[g] + v;
+    else w[g] = w[g] - v;
   }
 }
 
@@ -391,24 +421,35 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   const TW* T = table<TW>(p);
   const TW* ta = T + g.ax[axis].o_ta;
   const TW* tb = T + g.ax[axis].o_tb;
+  if (axis == 2 && sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
+    // lines too long to stage in shared memory: one thread per line from global memory
+    const int64_t rows = int64_t(mz) * my;
+    const int threads = 128;
+    const int blocks = int((rows + threads - 1) / threads);
+    if (op == SOLVE_INPLACE)
+      k_solve_strided<TW, SOLVE_INPLACE><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
+    else if (op == SOLVE_ADD)
+      k_solve_strided<TW, SOLVE_ADD><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
+    else
+      k_solve_strided<TW, SOLVE_SUB><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
+    return cudaGetLastError();
+  }
   if (axis == 2) {
     const int64_t rows = int64_t(mz) * my;
     const int pitch = mx | 1;
-    int R = int(std::min<size_t>(32, (96 * 1024) / (sizeof(TW) * pitch)));
-    R = std::max(R, 1);
-    const size_t sm = sizeof(TW) * size_t(R) * pitch;
+    // rows per CTA (one solving thread per row, 128 threads load and store):
+    // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
+    int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
+    R = std::max(1, R);
+    const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
     const int blocks = int((rows + R - 1) / R);
-    const int threads = 128;
-    if (op == SOLVE_INPLACE) {
-      cudaFuncSetAttribute(k_solve_contig<TW, SOLVE_INPLACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      k_solve_contig<TW, SOLVE_INPLACE><<<blocks, threads, sm, st>>>(f, w, mx, rows, mx, R, ta, tb);
-    } else if (op == SOLVE_ADD) {
-      cudaFuncSetAttribute(k_solve_contig<TW, SOLVE_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      k_solve_contig<TW, SOLVE_ADD><<<blocks, threads, sm, st>>>(f, w, mx, rows, mx, R, ta, tb);
-    } else {
-      cudaFuncSetAttribute(k_solve_contig<TW, SOLVE_SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      k_solve_contig<TW, SOLVE_SUB><<<blocks, threads, sm, st>>>(f, w, mx, rows, mx, R, ta, tb);
-    }
+    auto launch = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      kern<<<blocks, 128, sm, st>>>(f, w, mx, rows, mx, R, ta, tb);
+    };
+    if (op == SOLVE_INPLACE) launch(k_solve_contig<TW, SOLVE_INPLACE>);
+    else if (op == SOLVE_ADD) launch(k_solve_contig<TW, SOLVE_ADD>);
+    else launch(k_solve_contig<TW, SOLVE_SUB>);
     return cudaGetLastError();
   }
   int mline, inner;

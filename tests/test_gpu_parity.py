@@ -162,3 +162,16 @@ def test_invalid_arguments(ctx):
     with pytest.raises(mgr.MgrError):
         p.decompose(buf, buf[33 * 33:], ws[1:])  # misaligned workspace
     p.close()
+
+
+def test_long_1d_lines(ctx):
+    # x lines longer than the shared-memory staging of the contiguous solve
+    rng = np.random.default_rng(21)
+    u = rng.standard_normal(20001)
+    check_f64(ctx, u, [random_coords(rng, 20001)])
+    r = Runner(ctx, u.shape, None, -1, mgr.MGR_F32, mgr.MGR_PREC_NATIVE)
+    try:
+        got = r.decompose(u.astype(np.float32))
+        assert rel_linf(got, oracle.decompose(u.astype(np.float32).astype(np.float64))) <= TOL32
+    finally:
+        r.close()
