@@ -210,9 +210,15 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a)
     const TI* base = in + iplane(gz);
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
-      const int r0 = 2 * (warp * RPW + k);
-      if (vy0[k]) load_pair(sb + r0 * RC + cx0, base + ir0[k] + ic0, base + ir0[k] + ic1, vx0, vx1, icontig);
-      if (vy1[k]) load_pair(sb + (r0 + 1) * RC + cx0, base + ir1[k] + ic0, base + ir1[k] + ic1, vx0, vx1, icontig);
+      TI* d0 = sb + 2 * (warp * RPW + k) * RC + cx0;
+      if (vy0[k]) {
+        if (vx0) cp_async(d0, base + ir0[k] + ic0, int(sizeof(TI)));
+        if (vx1) cp_async(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)));
+      }
+      if (vy1[k]) {
+        if (vx0) cp_async(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)));
+        if (vx1) cp_async(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)));
+      }
     }
   };
   auto has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
@@ -434,11 +440,22 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a)
       const int j = warp * RPW + k;
       if (j < nby && kxo) {
         TS gc = TS(0), gf = TS(0);
+        const TS* gcol = gxb + (dyo[k] - 2) * 32 + lane;
+        if (kym[k] == 31u) {  // interior row: all five taps inside the grid
+          gc = ky[k][0] * gcol[0] + ky[k][1] * gcol[32] + ky[k][2] * gcol[64] + ky[k][3] * gcol[96] +
+               ky[k][4] * gcol[128];
+          if (hf) {
+            const TS* fcol = gcol + RR * 32;
+            gf = ky[k][0] * fcol[0] + ky[k][1] * fcol[32] + ky[k][2] * fcol[64] + ky[k][3] * fcol[96] +
+                 ky[k][4] * fcol[128];
+          }
+        } else {
 #pragma unroll
-        for (int o = 0; o < 5; ++o) {
-          if (kym[k] & (1u << o)) {
-            gc += ky[k][o] * gxb[(dyo[k] + o - 2) * 32 + lane];
-            if (hf) gf += ky[k][o] * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
+          for (int o = 0; o < 5; ++o) {
+            if (kym[k] & (1u << o)) {
+              gc += ky[k][o] * gxb[(dyo[k] + o - 2) * 32 + lane];
+              if (hf) gf += ky[k][o] * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
+            }
           }
         }
         acc0[k] += wzc[0] * gc;
