@@ -140,6 +140,49 @@ int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out
 int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
                        void* workspace, mgr_stream_t stream);
 
+/* ------------------------------------------------------------ batching */
+
+#define MGR_OP_DECOMPOSE 0
+#define MGR_OP_RECOMPOSE 1
+
+/* One field of a batch. */
+typedef struct {
+  int op;               /* MGR_OP_DECOMPOSE or MGR_OP_RECOMPOSE                      */
+  const mgr_plan* plan; /* the field's plan; every request of a submit shares the
+                           plan's dtype and precision                                */
+  const void* in;       /* DEVICE, field-sized                                       */
+  void* out;            /* DEVICE, field-sized, distinct from `in`                   */
+  uint64_t user_tag;    /* caller's bookkeeping; not interpreted                     */
+  int keep_resident;    /* serving layer only (mgr_serve_*); ignored by a batch      */
+} mgr_request;
+
+/* Batched refactoring of many independent fields of uneven sizes (the
+   batching pattern of the hot path): all fields advance level by level
+   together, each phase of the level loop (level pass, x/y/z solves,
+   interpolation) is ONE persistent launch whose CTAs walk a list of work
+   items across all fields, and the phase sequence is captured once into a
+   CUDA graph and replayed on later submits of the same request list.  The
+   level-pass tile shape and z-chunk length are chosen by the autotuner on
+   the first submit of a batch shape (analytic model ranks the candidates,
+   the top three are timed).  Decompositions run before recompositions; the
+   requests of one submit must be independent (no request reads another's
+   output).  The context allocates the workspaces (counted against its
+   memory budget; MGR_EBUDGET when a batch can never fit) and runs the work
+   on its own stream.  Returns after enqueueing; *ticket identifies the
+   submit for mgr_batch_poll. */
+int mgr_batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds (0: do not wait, < 0: no limit) for a
+   submit.  MGR_OK with *n_done = its request count when finished (the ticket
+   is then released), MGR_EPENDING (timeout 0) or MGR_ETIMEDOUT otherwise,
+   MGR_ENOTFOUND for an unknown or released ticket. */
+int mgr_batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_done);
+
+/* Text report of the autotuner's decisions (candidate tile shapes and their
+   measured times per batch shape).  Writes at most len bytes including the
+   terminating NUL; returns the full length. */
+int mgr_batch_tuning(mgr_ctx* ctx, char* buf, size_t len);
+
 /* ------------------------------------------------------------ profiling */
 
 /* One kernel launch of an operation, timed by CUDA events recorded on the

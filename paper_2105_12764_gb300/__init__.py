@@ -15,7 +15,7 @@ import os
 __all__ = [
     "MGR_OK", "MGR_EINVAL", "MGR_ENOMEM", "MGR_EBUDGET", "MGR_ECUDA", "MGR_EPENDING", "MGR_ETIMEDOUT",
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
-    "MgrError", "mgr_desc", "mgr_kernel_time", "lib", "library_path", "Context", "Plan", "EXPORTED",
+    "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE", "lib", "library_path", "Context", "Plan", "EXPORTED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,6 +54,19 @@ class mgr_kernel_time(ctypes.Structure):
     ]
 
 
+class mgr_request(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int),
+        ("plan", ctypes.c_void_p),
+        ("in_", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+        ("user_tag", ctypes.c_uint64),
+        ("keep_resident", ctypes.c_int),
+    ]
+
+
+MGR_OP_DECOMPOSE, MGR_OP_RECOMPOSE = 0, 1
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 # name -> (restype, argtypes): every entry point declared in include/mgr.h
@@ -73,6 +86,9 @@ EXPORTED = {
     "mgr_decompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
+    "mgr_batch_submit": (_i, [_vp, ctypes.POINTER(mgr_request), _i, ctypes.POINTER(ctypes.c_uint64)]),
+    "mgr_batch_poll": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_i)]),
+    "mgr_batch_tuning": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 
@@ -162,6 +178,35 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def batch_submit(self, requests):
+        """mgr_batch_submit; requests: iterable of (op, plan, in, out[, user_tag]).  Returns the ticket."""
+        reqs = list(requests)
+        arr = (mgr_request * max(1, len(reqs)))()
+        for i, r in enumerate(reqs):
+            op, plan, src, dst = r[:4]
+            arr[i].op = int(op)
+            arr[i].plan = plan.handle
+            arr[i].in_ = _ptr(src)
+            arr[i].out = _ptr(dst)
+            arr[i].user_tag = int(r[4]) if len(r) > 4 else i
+            arr[i].keep_resident = 0
+        t = ctypes.c_uint64()
+        _check("mgr_batch_submit", lib.mgr_batch_submit(self.handle, arr, len(reqs), ctypes.byref(t)))
+        return t.value
+
+    def batch_poll(self, ticket, timeout_us=-1):
+        """mgr_batch_poll: returns (code, n_done); raises only on errors other than pending/timeout."""
+        n = _i()
+        rc = lib.mgr_batch_poll(self.handle, int(ticket), int(timeout_us), ctypes.byref(n))
+        if rc not in (MGR_OK, MGR_EPENDING, MGR_ETIMEDOUT):
+            raise MgrError("mgr_batch_poll", rc)
+        return rc, n.value
+
+    def batch_tuning(self):
+        buf = ctypes.create_string_buffer(1 << 16)
+        lib.mgr_batch_tuning(self.handle, buf, len(buf))
+        return buf.value.decode()
 
 
 class Plan:

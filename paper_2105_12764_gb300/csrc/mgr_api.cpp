@@ -149,9 +149,27 @@ int mgr_shutdown(mgr_ctx* ctx) {
   if (!ctx) return MGR_EINVAL;
   if (ctx->live_plans.load() != 0) return MGR_EINVAL;
   cudaSetDevice(ctx->device);
+  mgr::batch_destroy(ctx);
   cudaDeviceSynchronize();
   delete ctx;
   return MGR_OK;
+}
+
+int mgr_batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket) {
+  try {
+    return mgr::batch_submit(ctx, reqs, n, ticket);
+  } catch (const std::bad_alloc&) {
+    return MGR_ENOMEM;
+  }
+}
+
+int mgr_batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_done) {
+  return mgr::batch_poll(ctx, ticket, timeout_us, n_done);
+}
+
+int mgr_batch_tuning(mgr_ctx* ctx, char* buf, size_t len) {
+  if (!ctx) return MGR_EINVAL;
+  return mgr::batch_tuning(ctx, buf, len);
 }
 
 int mgr_max_levels(const mgr_desc* desc, int* levels) {

@@ -1,0 +1,925 @@
+// mgr_batch.cu -- batched refactoring of many independent fields of uneven
+// sizes: one persistent, descriptor-driven launch per phase of the level
+// loop, the whole phase sequence captured once into a CUDA graph, and tile
+// shapes chosen by an autotuner.
+//
+// Phases follow the level loop of Sec. II.A for all fields at once, aligned by
+// depth d (depth 0 = every field's finest level): for decomposition, for d =
+// 0..D-1, the level pass (coefficients + load vector) of every field that has
+// a level L_f - d, then the x, y and z solves of those fields (the last axis
+// of each field adds the correction); then the coarsest-grid scatter.
+// Recomposition runs the depths in reverse with the interpolation pass.
+// Every phase is a single persistent launch whose CTAs walk a list of work
+// items (field descriptor, tile, z chunk); ordering between phases comes from
+// stream order inside the graph, so no CTA ever waits on another.
+//
+// Autotuning (Sec. III.B: an analytic model ranks the candidate launch
+// shapes, the top three are measured): candidates are the level-pass tile
+// (8 warps x 2 row pairs = 30x14 coarse nodes, or 4 warps x 2 = 30x6) and the
+// z-chunk length (8, 16 or 32 coarse planes).  The model charges each work
+// item the shared-memory slots it streams (halo and padding included) and
+// takes the longer of the memory time and the longest-processing-time
+// schedule of the items over the persistent CTAs; the three best are timed
+// on the real batch and the fastest is cached per batch shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <queue>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mgr_internal.h"
+
+namespace mgr {
+namespace {
+
+#include "mgr_device.cuh"
+#include "mgr_level.cuh"
+#include "mgr_solve.cuh"
+
+// ---------------------------------------------------------------------------
+// Descriptor-driven kernels (one CTA per work item, persistent grid)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void copy_words(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "descriptor size");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < int(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) kb_level(const LevelArgs<TS, TW>* __restrict__ args,
+                                                       const int4* __restrict__ items, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) LevelArgs<TS, TW> sa;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int4 it = items[i];
+    copy_words(&sa, args + it.x);
+    __syncthreads();
+    level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW>(sa, it.y, it.z, it.w, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) kb_interp(const InterpArgs<TS, TW>* __restrict__ args,
+                                                        const int4* __restrict__ items, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) InterpArgs<TS, TW> sa;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int4 it = items[i];
+    copy_words(&sa, args + it.x);
+    __syncthreads();
+    interp_body<NW, RPW, TD, TO, TS, TW>(sa, it.y, it.z, it.w, smem_raw);
+    __syncthreads();
+  }
+}
+
+template <typename TW>
+struct SolveDesc {
+  TW* f;
+  TW* w;
+  const TW* ta;
+  const TW* tb;
+  int64_t lstride, ostride, count, row_pitch;  // count: lines (strided) or rows (contiguous)
+  int mline, inner, op, R;
+};
+
+template <typename TW>
+__global__ void __launch_bounds__(128) kb_solve_strided(const SolveDesc<TW>* __restrict__ d,
+                                                        const int2* __restrict__ items, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int2 it = items[i];
+    const SolveDesc<TW> s = d[it.x];
+    const int64_t line = int64_t(it.y) * blockDim.x + threadIdx.x;
+    if (line < s.count) solve_strided_line<TW>(s.f, s.w, s.mline, s.lstride, s.inner, s.ostride, s.ta, s.tb, s.op, line);
+  }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) kb_solve_contig(const SolveDesc<TW>* __restrict__ d,
+                                                       const int2* __restrict__ items, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int2 it = items[i];
+    const SolveDesc<TW> s = d[it.x];
+    solve_contig_rows<TW>(s.f, s.w, s.mline, s.count, s.row_pitch, s.R, s.ta, s.tb, s.op, int64_t(it.y) * s.R,
+                          smem_raw);
+    __syncthreads();
+  }
+}
+
+template <typename TD, typename TW>
+struct CopyDesc {
+  TD* y;
+  TW* w;
+  int64_t y_sz, y_sy;
+  int3 n;
+  longlong3 s, N;
+  int dir;
+};
+
+template <typename TD, typename TW>
+__global__ void __launch_bounds__(256) kb_coarsest(const CopyDesc<TD, TW>* __restrict__ d, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const CopyDesc<TD, TW> c = d[i];
+    coarsest_copy<TD, TW>(c.y, c.y_sz, c.y_sy, c.w, c.n, c.s, c.N, c.dir, threadIdx.x, blockDim.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+template <typename T>
+const T* table_of(const mgr_plan* p);
+template <>
+const double* table_of<double>(const mgr_plan* p) { return p->tables.d64; }
+template <>
+const float* table_of<float>(const mgr_plan* p) { return p->tables.d32; }
+
+// Host staging of the device descriptor/item blob.
+struct Blob {
+  std::vector<unsigned char> host;
+  size_t put(const void* p, size_t n, size_t align = 16) {
+    size_t off = (host.size() + align - 1) & ~(align - 1);
+    host.resize(off + n);
+    std::memcpy(host.data() + off, p, n);
+    return off;
+  }
+};
+
+struct FieldRef {
+  const mgr_plan* p;
+  const void* in;
+  void* out;
+  char* ws;
+};
+
+// Level-pass tile candidates (NW warps x RPW row pairs); chunk lengths.
+struct TileCand {
+  int cfg;    // 0: 8 warps x 2 row pairs (30 x 14), 1: 4 warps x 2 (30 x 6)
+  int chunk;  // coarse z planes per work item
+};
+constexpr int kNumCfg = 2;
+inline int cfg_by(int cfg) { return cfg == 0 ? 14 : 6; }
+
+inline int ctas_per_sm(int cfg) { return cfg == 0 ? 2 : 4; }
+
+template <typename TD, typename TS, typename TW>
+struct Builder {
+  const std::vector<FieldRef>& fields;
+  int op;
+  TileCand cand;
+  int num_sms;
+  Blob blob;
+  struct PendingPhase {
+    const void* fn;
+    int kind;            // 0 level, 1 interp, 2 strided, 3 contig, 4 coarsest
+    size_t desc_off, items_off;
+    int n_items;
+    int block;
+    size_t smem;
+    int grid;
+  };
+  std::vector<PendingPhase> pending;
+  std::vector<std::function<void(cudaStream_t)>> copies;  // levels == 0 fields
+
+  Builder(const std::vector<FieldRef>& f, int o, TileCand c, int sms) : fields(f), op(o), cand(c), num_sms(sms) {}
+
+  static char* bufA(const FieldRef& fr) { return fr.ws; }
+  static char* bufB(const FieldRef& fr) { return fr.ws + fr.p->ws_a; }
+  static char* bufF(const FieldRef& fr) { return fr.ws + fr.p->ws_a + fr.p->ws_b; }
+
+  LevelArgs<TS, TW> level_args(const FieldRef& fr, int l) const {
+    const mgr_plan* p = fr.p;
+    const LevelGeom& g = p->geom[l];
+    LevelArgs<TS, TW> a{};
+    const TS* T = table_of<TS>(p);
+    for (int k = 0; k < 3; ++k) {
+      a.n[k] = g.ax[k].n;
+      a.m[k] = g.ax[k].m;
+      a.s[k] = g.ax[k].s;
+      a.N[k] = g.ax[k].N;
+      a.wa[k] = T + g.ax[k].o_wa;
+      a.wb[k] = T + g.ax[k].o_wb;
+      a.k[k] = T + g.ax[k].o_k;
+    }
+    a.y_sz = p->full[1] * p->full[2];
+    a.y_sy = p->full[2];
+    a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
+    a.c_sy = g.ax[2].m;
+    a.qz_chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+    return a;
+  }
+
+  // Level-pass phase for all fields at depth d.
+  template <int MODE, typename TI>
+  void level_phase(int d, bool first_dec) {
+    std::vector<LevelArgs<TS, TW>> descs;
+    std::vector<int4> items;
+    const int BX = 30, BY = cfg_by(cand.cfg);
+    for (const FieldRef& fr : fields) {
+      const int L = fr.p->levels;
+      if (L <= d) continue;
+      const int l = L - d;
+      LevelArgs<TS, TW> a = level_args(fr, l);
+      if (MODE == 0) {
+        char* nxt = ((L - l) % 2 == 0) ? bufA(fr) : bufB(fr);
+        char* cur = ((L - l - 1) % 2 == 0) ? bufA(fr) : bufB(fr);
+        a.y = fr.out;
+        a.w = reinterpret_cast<TW*>(nxt);
+        a.f = reinterpret_cast<TW*>(bufF(fr));
+        a.write_y = 1;
+        if (l == L) {
+          a.in = fr.in;
+          a.in_full = 1;
+          a.in_sz = a.y_sz;
+          a.in_sy = a.y_sy;
+        } else {
+          const LevelGeom& g = fr.p->geom[l];
+          a.in = cur;
+          a.in_full = 0;
+          a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
+          a.in_sy = g.ax[2].n;
+        }
+      } else {
+        a.in = fr.in;
+        a.in_full = 1;
+        a.in_sz = a.y_sz;
+        a.in_sy = a.y_sy;
+        a.f = reinterpret_cast<TW*>(bufF(fr));
+        a.w = nullptr;
+        a.y = nullptr;
+        a.write_y = 0;
+      }
+      const int di = int(descs.size());
+      descs.push_back(a);
+      const int gx = (a.m[2] + BX - 1) / BX, gy = (a.m[1] + BY - 1) / BY, gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+      for (int z = 0; z < gz; ++z)
+        for (int y = 0; y < gy; ++y)
+          for (int x = 0; x < gx; ++x) items.push_back(make_int4(di, x, y, z));
+    }
+    (void)first_dec;
+    if (items.empty()) return;
+    PendingPhase ph{};
+    ph.kind = 0;
+    ph.desc_off = blob.put(descs.data(), descs.size() * sizeof(descs[0]));
+    ph.items_off = blob.put(items.data(), items.size() * sizeof(int4));
+    ph.n_items = int(items.size());
+    if (cand.cfg == 0) {
+      using C = LevelCfg<TS>;
+      ph.fn = reinterpret_cast<const void*>(kb_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>);
+      ph.block = C::NW * 32;
+      ph.smem = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
+    } else {
+      constexpr int ST = LevelCfg<TS>::STAGES;
+      ph.fn = reinterpret_cast<const void*>(kb_level<MODE, 4, 2, ST, TI, TD, TS, TW>);
+      ph.block = 128;
+      ph.smem = level_smem_bytes<4, 2, ST, TI, TS>();
+    }
+    ph.grid = std::min(ph.n_items, num_sms * ctas_per_sm(cand.cfg));
+    pending.push_back(ph);
+  }
+
+  template <typename TO>
+  void interp_phase(int d) {
+    std::vector<InterpArgs<TS, TW>> descs;
+    std::vector<int4> items;
+    constexpr int NW = 8, RPW = 2, BY = NW * RPW;
+    for (const FieldRef& fr : fields) {
+      const int L = fr.p->levels;
+      if (L <= d) continue;
+      const int l = L - d;
+      const mgr_plan* p = fr.p;
+      const LevelGeom& g = p->geom[l];
+      const TS* T = table_of<TS>(p);
+      InterpArgs<TS, TW> a{};
+      for (int k = 0; k < 3; ++k) {
+        a.n[k] = g.ax[k].n;
+        a.m[k] = g.ax[k].m;
+        a.s[k] = g.ax[k].s;
+        a.N[k] = g.ax[k].N;
+        a.wa[k] = T + g.ax[k].o_wa;
+        a.wb[k] = T + g.ax[k].o_wb;
+      }
+      // the coarse values of level l-1 and the level-l destination
+      char* cur = ((L - l) % 2 == 0) ? bufA(fr) : bufB(fr);
+      char* nxt = ((L - l + 1) % 2 == 0) ? bufA(fr) : bufB(fr);
+      a.c = fr.in;
+      a.y_sz = p->full[1] * p->full[2];
+      a.y_sy = p->full[2];
+      a.w = reinterpret_cast<const TW*>(cur);
+      a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
+      a.c_sy = g.ax[2].m;
+      const bool last = (l == L);
+      a.out = last ? fr.out : static_cast<void*>(nxt);
+      a.out_full = last ? 1 : 0;
+      a.o_sz = last ? a.y_sz : int64_t(g.ax[1].n) * g.ax[2].n;
+      a.o_sy = last ? a.y_sy : int64_t(g.ax[2].n);
+      a.qz_chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+      const int di = int(descs.size());
+      descs.push_back(a);
+      const int gx = (a.m[2] + 31) / 32, gy = (a.m[1] + BY - 1) / BY, gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+      for (int z = 0; z < gz; ++z)
+        for (int y = 0; y < gy; ++y)
+          for (int x = 0; x < gx; ++x) items.push_back(make_int4(di, x, y, z));
+    }
+    if (items.empty()) return;
+    PendingPhase ph{};
+    ph.kind = 1;
+    ph.desc_off = blob.put(descs.data(), descs.size() * sizeof(descs[0]));
+    ph.items_off = blob.put(items.data(), items.size() * sizeof(int4));
+    ph.n_items = int(items.size());
+    ph.fn = reinterpret_cast<const void*>(kb_interp<NW, RPW, TD, TO, TS, TW>);
+    ph.block = NW * 32;
+    ph.smem = interp_smem_bytes<NW, RPW, TD, TW>();
+    ph.grid = std::min(ph.n_items, num_sms * 2);
+    pending.push_back(ph);
+  }
+
+  // Solves of all fields at depth d along `axis`; fields whose last active
+  // axis is `axis` apply the correction with `final_op`.
+  void solve_phase(int d, int axis, int final_op) {
+    std::vector<SolveDesc<TW>> sdesc, cdesc;
+    std::vector<int2> sitems, citems;
+    size_t csmem = 0;
+    for (const FieldRef& fr : fields) {
+      const int L = fr.p->levels;
+      if (L <= d) continue;
+      const int l = L - d;
+      const LevelGeom& g = fr.p->geom[l];
+      if (!g.ax[axis].active) continue;
+      int last = -1;
+      for (int a2 = 2; a2 >= 0; --a2)
+        if (g.ax[a2].active) last = a2;
+      const TW* T = table_of<TW>(fr.p);
+      const int mz = g.ax[0].m, my = g.ax[1].m, mx = g.ax[2].m;
+      SolveDesc<TW> s{};
+      s.f = reinterpret_cast<TW*>(bufF(fr));
+      s.w = reinterpret_cast<TW*>(((L - l) % 2 == 0) ? bufA(fr) : bufB(fr));
+      s.ta = T + g.ax[axis].o_ta;
+      s.tb = T + g.ax[axis].o_tb;
+      s.op = (axis == last) ? final_op : SOLVE_INPLACE;
+      const size_t stage = sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx));
+      if (axis == 2 && stage <= 96 * 1024) {
+        const int pitch = mx | 1;
+        int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
+        R = std::max(1, R);
+        s.mline = mx;
+        s.count = int64_t(mz) * my;
+        s.row_pitch = mx;
+        s.R = R;
+        csmem = std::max(csmem, sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx)));
+        const int di = int(cdesc.size());
+        cdesc.push_back(s);
+        const int64_t blocks = (s.count + R - 1) / R;
+        for (int64_t b = 0; b < blocks; ++b) citems.push_back(make_int2(di, int(b)));
+      } else {
+        if (axis == 2) {
+          s.mline = mx; s.lstride = 1; s.inner = 1; s.ostride = mx; s.count = int64_t(mz) * my;
+        } else if (axis == 1) {
+          s.mline = my; s.lstride = mx; s.inner = mx; s.ostride = int64_t(my) * mx; s.count = int64_t(mz) * mx;
+        } else {
+          s.mline = mz; s.lstride = int64_t(my) * mx; s.inner = mx; s.ostride = mx; s.count = int64_t(my) * mx;
+        }
+        const int di = int(sdesc.size());
+        sdesc.push_back(s);
+        const int64_t blocks = (s.count + 127) / 128;
+        for (int64_t b = 0; b < blocks; ++b) sitems.push_back(make_int2(di, int(b)));
+      }
+    }
+    if (!citems.empty()) {
+      PendingPhase ph{};
+      ph.kind = 3;
+      ph.desc_off = blob.put(cdesc.data(), cdesc.size() * sizeof(cdesc[0]));
+      ph.items_off = blob.put(citems.data(), citems.size() * sizeof(int2));
+      ph.n_items = int(citems.size());
+      ph.fn = reinterpret_cast<const void*>(kb_solve_contig<TW>);
+      ph.block = 128;
+      ph.smem = csmem;
+      ph.grid = std::min<int>(ph.n_items, num_sms * 6);
+      pending.push_back(ph);
+    }
+    if (!sitems.empty()) {
+      PendingPhase ph{};
+      ph.kind = 2;
+      ph.desc_off = blob.put(sdesc.data(), sdesc.size() * sizeof(sdesc[0]));
+      ph.items_off = blob.put(sitems.data(), sitems.size() * sizeof(int2));
+      ph.n_items = int(sitems.size());
+      ph.fn = reinterpret_cast<const void*>(kb_solve_strided<TW>);
+      ph.block = 128;
+      ph.smem = 0;
+      ph.grid = std::min<int>(ph.n_items, num_sms * 8);
+      pending.push_back(ph);
+    }
+  }
+
+  void coarsest_phase(int dir) {
+    std::vector<CopyDesc<TD, TW>> descs;
+    for (const FieldRef& fr : fields) {
+      const mgr_plan* p = fr.p;
+      const int L = p->levels;
+      if (L == 0) continue;
+      CopyDesc<TD, TW> c{};
+      c.y = static_cast<TD*>(dir == 1 ? fr.out : const_cast<void*>(fr.in));
+      // level-0 values: where the last decomposition level wrote them / where
+      // the first recomposition level reads them (same ping-pong rule)
+      c.w = reinterpret_cast<TW*>((L % 2 == 1) ? bufA(fr) : bufB(fr));
+      c.y_sz = p->full[1] * p->full[2];
+      c.y_sy = p->full[2];
+      c.n = make_int3(int(p->coarsest[0]), int(p->coarsest[1]), int(p->coarsest[2]));
+      const int64_t s0 = int64_t(1) << L;
+      c.s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
+      c.N = make_longlong3(p->full[0], p->full[1], p->full[2]);
+      c.dir = dir;
+      descs.push_back(c);
+    }
+    if (descs.empty()) return;
+    PendingPhase ph{};
+    ph.kind = 4;
+    ph.desc_off = blob.put(descs.data(), descs.size() * sizeof(descs[0]));
+    ph.items_off = 0;
+    ph.n_items = int(descs.size());
+    ph.fn = reinterpret_cast<const void*>(kb_coarsest<TD, TW>);
+    ph.block = 256;
+    ph.smem = 0;
+    ph.grid = std::min(ph.n_items, num_sms * 8);
+    pending.push_back(ph);
+  }
+
+  void build() {
+    int D = 0;
+    for (const FieldRef& fr : fields) D = std::max(D, fr.p->levels);
+    for (const FieldRef& fr : fields) {
+      if (fr.p->levels == 0 && fr.in != fr.out) {
+        const FieldRef f = fr;
+        copies.push_back([f](cudaStream_t st) {
+          cudaMemcpyAsync(f.out, f.in, size_t(f.p->count) * f.p->elem, cudaMemcpyDeviceToDevice, st);
+        });
+      }
+    }
+    if (op == 0) {
+      for (int d = 0; d < D; ++d) {
+        if (d == 0) level_phase<0, TD>(d, true);
+        else level_phase<0, TW>(d, false);
+        solve_phase(d, 2, SOLVE_ADD);
+        solve_phase(d, 1, SOLVE_ADD);
+        solve_phase(d, 0, SOLVE_ADD);
+      }
+      coarsest_phase(1);
+    } else {
+      coarsest_phase(0);
+      for (int d = D - 1; d >= 0; --d) {
+        level_phase<1, TD>(d, false);
+        solve_phase(d, 2, SOLVE_SUB);
+        solve_phase(d, 1, SOLVE_SUB);
+        solve_phase(d, 0, SOLVE_SUB);
+        if (d == 0) interp_phase<TD>(d);
+        else interp_phase<TW>(d);
+      }
+    }
+  }
+
+  // Estimated time of this candidate (model of Sec. III.B, restated): every
+  // level-pass item streams RR x RC slots per plane pair (halo and padding
+  // included); the phase takes the longer of that traffic at HBM speed and
+  // the LPT schedule of the items over the persistent CTAs.
+  double model_cost(double hbm_bytes_per_us) const {
+    double total = 0;
+    const int BY = cfg_by(cand.cfg);
+    const int RR = 2 * (BY + 2), RC = 64;
+    const int slots = num_sms * ctas_per_sm(cand.cfg);
+    const double t_iter_us = (cand.cfg == 0 ? 1.6 : 1.0);
+    int D = 0;
+    for (const FieldRef& fr : fields) D = std::max(D, fr.p->levels);
+    for (int d = 0; d < D; ++d) {
+      std::vector<double> jobs;
+      double bytes = 0;
+      for (const FieldRef& fr : fields) {
+        const int L = fr.p->levels;
+        if (L <= d) continue;
+        const LevelGeom& g = fr.p->geom[L - d];
+        const int chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+        const int gx = (g.ax[2].m + 29) / 30, gy = (g.ax[1].m + BY - 1) / BY;
+        const int gz = (g.ax[0].m + chunk - 1) / chunk;
+        for (int z = 0; z < gz; ++z) {
+          const int planes = std::min(chunk, g.ax[0].m - z * chunk) + 1;
+          for (int i = 0; i < gx * gy; ++i) {
+            jobs.push_back(planes * t_iter_us + 2.0);
+            bytes += double(planes) * 2.0 * RR * RC * fr.p->elem;
+          }
+        }
+      }
+      std::sort(jobs.begin(), jobs.end(), std::greater<double>());
+      std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+      for (int i = 0; i < std::min<int>(slots, int(jobs.size())); ++i) q.push(0.0);
+      for (double j : jobs) {
+        double t = q.top();
+        q.pop();
+        q.push(t + j);
+      }
+      double makespan = 0;
+      while (!q.empty()) {
+        makespan = std::max(makespan, q.top());
+        q.pop();
+      }
+      total += std::max(makespan, bytes / hbm_bytes_per_us);
+    }
+    return total;
+  }
+};
+
+// Launch-ready batch: device blob (descriptors, items) and the phase list.
+struct BatchExec {
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  struct L {
+    const void* fn;
+    int kind;
+    const void* desc;
+    const void* items;
+    int n;
+    dim3 grid, block;
+    size_t smem;
+  };
+  std::vector<L> launches;
+  std::vector<std::function<void(cudaStream_t)>> copies;
+  cudaGraphExec_t graph = nullptr;
+  ~BatchExec() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (dev) cudaFree(dev);
+  }
+  cudaError_t enqueue(cudaStream_t st) const {
+    for (auto& c : copies) c(st);
+    for (const L& l : launches) {
+      if (l.smem > 48 * 1024) cudaFuncSetAttribute(l.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(l.smem));
+      if (l.kind == 4) {
+        void* args[] = {const_cast<void**>(&l.desc), const_cast<int*>(&l.n)};
+        cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
+        if (e != cudaSuccess) return e;
+      } else {
+        void* args[] = {const_cast<void**>(&l.desc), const_cast<void**>(&l.items), const_cast<int*>(&l.n)};
+        cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaGetLastError();
+  }
+};
+
+template <typename TD, typename TS, typename TW>
+int make_exec(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms, std::unique_ptr<BatchExec>& out) {
+  Builder<TD, TS, TW> b(fields, op, cand, num_sms);
+  b.build();
+  auto ex = std::make_unique<BatchExec>();
+  ex->dev_bytes = std::max<size_t>(b.blob.host.size(), 16);
+  if (cudaMalloc(&ex->dev, ex->dev_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ENOMEM;
+  }
+  if (!b.blob.host.empty() &&
+      cudaMemcpy(ex->dev, b.blob.host.data(), b.blob.host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MGR_ECUDA;
+  char* base = static_cast<char*>(ex->dev);
+  for (auto& ph : b.pending) {
+    BatchExec::L l{};
+    l.fn = ph.fn;
+    l.kind = ph.kind;
+    l.desc = base + ph.desc_off;
+    l.items = base + ph.items_off;
+    l.n = ph.n_items;
+    l.grid = dim3(std::max(1, ph.grid));
+    l.block = dim3(ph.block);
+    l.smem = ph.smem;
+    ex->launches.push_back(l);
+  }
+  ex->copies = std::move(b.copies);
+  out = std::move(ex);
+  return MGR_OK;
+}
+
+template <typename TD, typename TS, typename TW>
+double model_of(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms) {
+  Builder<TD, TS, TW> b(fields, op, cand, num_sms);
+  return b.model_cost(6.79e6 * 0.6);  // bytes per microsecond at ~60% of the measured copy bandwidth
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batch state owned by the context
+// ---------------------------------------------------------------------------
+struct BatchState {
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  uint64_t next_ticket = 1;
+  struct Ticket {
+    cudaEvent_t done;
+    int n;
+  };
+  std::map<uint64_t, Ticket> tickets;
+  // executable batches keyed by the request list
+  struct Entry {
+    std::string key;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    std::unique_ptr<BatchExec> exec;
+    uint64_t last_use = 0;
+  };
+  std::vector<std::unique_ptr<Entry>> entries;
+  size_t held_bytes = 0;
+  uint64_t clock = 0;
+  // autotune decisions keyed by the batch shape
+  std::map<std::string, TileCand> tuned;
+  std::map<std::string, std::vector<std::pair<TileCand, double>>> tune_log;
+};
+
+namespace {
+
+std::string shape_key(const std::vector<const mgr_plan*>& plans, int op, int form) {
+  std::string k = std::to_string(op) + ":" + std::to_string(form) + ":";
+  std::vector<std::string> parts;
+  for (const mgr_plan* p : plans) {
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "%lldx%lldx%lld/%d", (long long)p->full[0], (long long)p->full[1],
+                  (long long)p->full[2], p->levels);
+    parts.push_back(buf);
+  }
+  std::sort(parts.begin(), parts.end());
+  for (auto& s : parts) k += s + ",";
+  return k;
+}
+
+template <typename TD, typename TS, typename TW>
+int exec_for(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fields, int op, const std::string& skey,
+             TileCand cand, std::unique_ptr<BatchExec>& out) {
+  (void)B;
+  (void)skey;
+  return make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, out);
+}
+
+// Time one candidate on the real batch (graph-less, after one warm-up run).
+template <typename TD, typename TS, typename TW>
+double time_candidate(mgr_ctx* ctx, const std::vector<FieldRef>& fields, int op, TileCand cand, cudaStream_t st) {
+  std::unique_ptr<BatchExec> ex;
+  if (make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ex) != MGR_OK) return 1e30;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  ex->enqueue(st);
+  cudaEventRecord(a, st);
+  ex->enqueue(st);
+  cudaEventRecord(b, st);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaGetLastError();
+  return ms;
+}
+
+template <typename TD, typename TS, typename TW>
+TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fields, int op, const std::string& skey) {
+  auto it = B.tuned.find(skey);
+  if (it != B.tuned.end()) return it->second;
+  std::vector<std::pair<double, TileCand>> ranked;
+  for (int cfg = 0; cfg < kNumCfg; ++cfg)
+    for (int chunk : {8, 16, 32}) {
+      TileCand c{cfg, chunk};
+      ranked.push_back({model_of<TD, TS, TW>(fields, op, c, ctx->num_sms), c});
+    }
+  std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  TileCand best = ranked[0].second;
+  double best_ms = 1e30;
+  std::vector<std::pair<TileCand, double>> log;
+  for (int i = 0; i < 3 && i < int(ranked.size()); ++i) {
+    const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, ranked[i].second, B.stream);
+    log.push_back({ranked[i].second, ms});
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ranked[i].second;
+    }
+  }
+  B.tuned[skey] = best;
+  B.tune_log[skey] = log;
+  return best;
+}
+
+template <typename TD, typename TS, typename TW>
+int run_group(mgr_ctx* ctx, BatchState& B, const std::vector<const mgr_request*>& reqs, int op) {
+  // workspace / executable lookup keyed by the exact request list
+  std::string key = std::to_string(op) + "|";
+  std::vector<const mgr_plan*> plans;
+  size_t ws_total = 0;
+  for (const mgr_request* r : reqs) {
+    char buf[80];
+    std::snprintf(buf, sizeof(buf), "%p:%p:%p;", (const void*)r->plan, r->in, r->out);
+    key += buf;
+    plans.push_back(r->plan);
+    ws_total += (r->plan->ws_bytes + 255) & ~size_t(255);
+  }
+  const int form = reqs[0]->plan->form;
+  const std::string skey = shape_key(plans, op, form);
+  BatchState::Entry* ent = nullptr;
+  for (auto& e : B.entries)
+    if (e->key == key) ent = e.get();
+  if (!ent) {
+    if (ctx->budget && ws_total > ctx->budget) return MGR_EBUDGET;
+    // evict least recently used entries until the new workspace fits the budget
+    while (ctx->budget && B.held_bytes + ws_total > ctx->budget && !B.entries.empty()) {
+      cudaStreamSynchronize(B.stream);
+      auto victim = std::min_element(B.entries.begin(), B.entries.end(),
+                                     [](const auto& x, const auto& y) { return x->last_use < y->last_use; });
+      B.held_bytes -= (*victim)->ws_bytes;
+      cudaFree((*victim)->ws);
+      B.entries.erase(victim);
+    }
+    auto e = std::make_unique<BatchState::Entry>();
+    e->key = key;
+    e->ws_bytes = std::max<size_t>(ws_total, 256);
+    if (cudaMalloc(&e->ws, e->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return MGR_ENOMEM;
+    }
+    std::vector<FieldRef> fields;
+    char* w = static_cast<char*>(e->ws);
+    for (const mgr_request* r : reqs) {
+      fields.push_back(FieldRef{r->plan, r->in, r->out, w});
+      w += (r->plan->ws_bytes + 255) & ~size_t(255);
+    }
+    const TileCand cand = autotune<TD, TS, TW>(ctx, B, fields, op, skey);
+    int rc = exec_for<TD, TS, TW>(ctx, B, fields, op, skey, cand, e->exec);
+    if (rc != MGR_OK) {
+      cudaFree(e->ws);
+      return rc;
+    }
+    // capture the phase sequence once
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaFree(e->ws);
+      return MGR_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      cudaError_t e2 = e->exec->enqueue(cs);
+      ce = cudaStreamEndCapture(cs, &g);
+      if (e2 != cudaSuccess) ce = e2;
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e->exec->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(e->ws);
+      return MGR_ECUDA;
+    }
+    B.held_bytes += e->ws_bytes;
+    ent = e.get();
+    B.entries.push_back(std::move(e));
+  }
+  ent->last_use = ++B.clock;
+  return cudaGraphLaunch(ent->exec->graph, B.stream) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+}
+
+BatchState* state_of(mgr_ctx* ctx) {
+  if (!ctx->batch) {
+    auto* s = new BatchState();
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return nullptr;
+    }
+    ctx->batch = s;
+  }
+  return static_cast<BatchState*>(ctx->batch);
+}
+
+}  // namespace
+
+void batch_destroy(mgr_ctx* ctx) {
+  if (!ctx->batch) return;
+  BatchState* s = static_cast<BatchState*>(ctx->batch);
+  cudaStreamSynchronize(s->stream);
+  for (auto& t : s->tickets) cudaEventDestroy(t.second.done);
+  for (auto& e : s->entries) cudaFree(e->ws);
+  s->entries.clear();
+  cudaStreamDestroy(s->stream);
+  delete s;
+  ctx->batch = nullptr;
+}
+
+int batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket) {
+  if (!ctx || !ticket || n < 0 || (n > 0 && !reqs)) return MGR_EINVAL;
+  *ticket = 0;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return MGR_ECUDA;
+  BatchState* B = state_of(ctx);
+  if (!B) return MGR_ECUDA;
+  std::lock_guard<std::mutex> lk(B->mu);
+  std::vector<const mgr_request*> dec, rec;
+  int form = -1;
+  for (int i = 0; i < n; ++i) {
+    const mgr_request& r = reqs[i];
+    if (!r.plan || !r.in || !r.out || r.in == r.out) return MGR_EINVAL;
+    if (r.plan->ctx != ctx) return MGR_EINVAL;
+    if (form < 0) form = r.plan->form;
+    if (r.plan->form != form) return MGR_EINVAL;
+    if (r.op == 0) dec.push_back(&r);
+    else if (r.op == 1) rec.push_back(&r);
+    else return MGR_EINVAL;
+  }
+  int rc = MGR_OK;
+  for (int pass = 0; pass < 2 && rc == MGR_OK; ++pass) {
+    auto& grp = pass == 0 ? dec : rec;
+    if (grp.empty()) continue;
+    switch (form) {
+      case kFormF64: rc = run_group<double, double, double>(ctx, *B, grp, pass); break;
+      case kFormF32: rc = run_group<float, float, float>(ctx, *B, grp, pass); break;
+      default: rc = run_group<float, float, double>(ctx, *B, grp, pass); break;
+    }
+  }
+  if (rc != MGR_OK) return rc;
+  BatchState::Ticket t{};
+  if (cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) return MGR_ECUDA;
+  cudaEventRecord(t.done, B->stream);
+  t.n = n;
+  *ticket = B->next_ticket++;
+  B->tickets[*ticket] = t;
+  return MGR_OK;
+}
+
+int batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_done) {
+  if (!ctx || !n_done) return MGR_EINVAL;
+  *n_done = 0;
+  BatchState* B = static_cast<BatchState*>(ctx->batch);
+  if (!B) return MGR_ENOTFOUND;
+  cudaEvent_t ev;
+  int n;
+  {
+    std::lock_guard<std::mutex> lk(B->mu);
+    auto it = B->tickets.find(ticket);
+    if (it == B->tickets.end()) return MGR_ENOTFOUND;
+    ev = it->second.done;
+    n = it->second.n;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) {
+      cudaGetLastError();
+      return MGR_ECUDA;
+    }
+    if (timeout_us == 0) return MGR_EPENDING;
+    const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0);
+    if (timeout_us > 0 && el.count() >= timeout_us) return MGR_ETIMEDOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  {
+    std::lock_guard<std::mutex> lk(B->mu);
+    auto it = B->tickets.find(ticket);
+    if (it != B->tickets.end()) {
+      cudaEventDestroy(it->second.done);
+      B->tickets.erase(it);
+    }
+  }
+  *n_done = n;
+  return MGR_OK;
+}
+
+int batch_tuning(mgr_ctx* ctx, char* buf, size_t len) {
+  BatchState* B = ctx ? static_cast<BatchState*>(ctx->batch) : nullptr;
+  std::string s;
+  if (B) {
+    std::lock_guard<std::mutex> lk(B->mu);
+    for (auto& kv : B->tune_log) {
+      s += "shape[" + std::to_string(kv.first.size()) + " chars]";
+      const TileCand c = B->tuned[kv.first];
+      char line[128];
+      std::snprintf(line, sizeof(line), " chosen tile=%s chunk=%d;", c.cfg == 0 ? "30x14" : "30x6", c.chunk);
+      s += line;
+      for (auto& m : kv.second) {
+        std::snprintf(line, sizeof(line), " [%s/%d: %.3f ms]", m.first.cfg == 0 ? "30x14" : "30x6", m.first.chunk,
+                      m.second);
+        s += line;
+      }
+      s += "\n";
+    }
+  }
+  if (buf && len) {
+    std::snprintf(buf, len, "%s", s.c_str());
+  }
+  return int(s.size());
+}
+
+}  // namespace mgr

@@ -58,37 +58,9 @@ inline void rec_end(cudaStream_t st, const char* name, int level, double bytes, 
   r.flops = flops;
 }
 
-__device__ __forceinline__ int pidx(int q, int n) { return min(2 * q, n - 1); }
-__device__ __forceinline__ bool is_coarse(int i, int n) { return ((i & 1) == 0) || (i == n - 1); }
-__device__ __forceinline__ int cidx(int i) { return (i + 1) >> 1; }
-// first fine node of the stencil region of coarse node q0, moved down to a coarse node
-__device__ __forceinline__ int region_start(int q0, int n) {
-  const int r = pidx(q0, n) - 2;
-  return (r & 1) ? r - 1 : r;
-}
-__device__ __forceinline__ int64_t fmap(int i, int64_t s, int64_t N) {
-  int64_t f = int64_t(i) * s;
-  return f < N - 1 ? f : N - 1;
-}
-
-// Asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses
-// aligned to the copy size).
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
-  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if (bytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
+#include "mgr_device.cuh"
 #include "mgr_level.cuh"
+#include "mgr_solve.cuh"
 
 // ---------------------------------------------------------------------------
 // In-place decomposition of the finest level: coefficients written pointwise
@@ -125,142 +97,6 @@ __global__ void k_coef_inplace(TD* y, int nz, int ny, int nx, const TS* waz, con
 }
 
 // ---------------------------------------------------------------------------
-// Thomas recurrences (scaled LU, one FMA per step and direction)
-// ---------------------------------------------------------------------------
-enum { SOLVE_INPLACE = 0, SOLVE_ADD = 1, SOLVE_SUB = 2 };
-
-// Lines along a strided axis: element q of line (o, i) at o*ostride + i + q*lstride.
-template <typename TW, int OP>
-__global__ void __launch_bounds__(256) k_solve_strided(TW* __restrict__ f, TW* __restrict__ w, int mline,
-                                                       int64_t lstride, int inner, int64_t outer, int64_t ostride,
-                                                       const TW* __restrict__ ta, const TW* __restrict__ tb) {
-  const int64_t id = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (id >= int64_t(inner) * outer) return;
-  const int i = int(id % inner);
-  const int64_t o = id / inner;
-  TW* fl = f + o * ostride + i;
-  constexpr int U = 8;
-  TW prev = TW(0);
-  for (int q0 = 0; q0 < mline; q0 += U) {
-    TW buf[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (q0 + u < mline) buf[u] = fl[int64_t(q0 + u) * lstride];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (q0 + u < mline) {
-        prev = buf[u] - ta[q0 + u] * prev;
-        fl[int64_t(q0 + u) * lstride] = prev;
-      }
-  }
-  TW* wl = w + o * ostride + i;
-  TW next = TW(0);
-  for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
-    TW buf[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (q1 - u >= 0) buf[u] = fl[int64_t(q1 - u) * lstride];
-    TW wv[U];
-    if (OP != SOLVE_INPLACE) {
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q1 - u >= 0) wv[u] = wl[int64_t(q1 - u) * lstride];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (q1 - u >= 0) {
-        const int q = q1 - u;
-        next = buf[u] - tb[q] * next;
-        if (OP == SOLVE_INPLACE) fl[int64_t(q) * lstride] = next;
-        else if (OP == SOLVE_ADD) wl[int64_t(q) * lstride] = wv[u] + next;
-        else wl[int64_t(q) * lstride] = wv[u] - next;
-      }
-  }
-}
-
-// Lines along the contiguous axis: blockDim.x rows of length mline staged in
-// shared memory with coalesced loads/stores; each thread then runs the
-// recurrences of its own row in chunks of 8 (eight independent loads, eight
-// dependent FMAs, eight stores), with the recurrence coefficients staged
-// once per CTA.
-template <typename TW, int OP>
-__global__ void __launch_bounds__(128) k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows,
-                                                      int64_t row_pitch, int R, const TW* __restrict__ ta,
-                                                      const TW* __restrict__ tb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int pitch = mline | 1;  // odd pitch spreads the rows of a warp over the banks
-  TW* s = reinterpret_cast<TW*>(smem_raw);  // [R][pitch]
-  TW* sa = s + R * pitch;                   // [mline]
-  TW* sb = sa + mline;                      // [mline]
-  const int64_t r0 = blockIdx.x * int64_t(R);
-  const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
-  for (int q = threadIdx.x; q < mline; q += blockDim.x) {
-    sa[q] = ta[q];
-    sb[q] = tb[q];
-  }
-  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
-    const int r = e / mline, c = e - r * mline;
-    s[r * pitch + c] = f[(r0 + r) * row_pitch + c];
-  }
-  __syncthreads();
-  if (threadIdx.x < nr) {
-    TW* l = s + threadIdx.x * pitch;
-    constexpr int U = 8;
-    TW prev = TW(0);
-    for (int q0 = 0; q0 < mline; q0 += U) {
-      TW v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = (q0 + u < mline) ? l[q0 + u] : TW(0);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        prev = v[u] - sa[min(q0 + u, mline - 1)] * prev;
-        v[u] = prev;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q0 + u < mline) l[q0 + u] = v[u];
-    }
-    TW next = TW(0);
-    for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
-      TW v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = (q1 - u >= 0) ? l[q1 - u] : TW(0);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        next = v[u] - sb[max(q1 - u, 0)] * next;
-        v[u] = next;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q1 - u >= 0) l[q1 - u] = v[u];
-    }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
-    const int r = e / mline, c = e - r * mline;
-    const int64_t g = (r0 + r) * row_pitch + c;
-    const TW v = s[r * pitch + c];
-    if (OP == SOLVE_INPLACE) f[g] = v;
-    else if (OP == SOLVE_ADD) w[g] = w[g] + v;
-    else w[g] = w[g] - v;
-  }
-}
-
-// Coarsest grid <-> nodal positions (dir 0: gather nodal -> compact; 1: scatter)
-template <typename TD, typename TW>
-__global__ void k_coarsest(TD* y, int64_t y_sz, int64_t y_sy, TW* w, int3 n, longlong3 s, longlong3 N, int dir) {
-  const int64_t total = int64_t(n.x) * n.y * n.z;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
-    const int gx = int(e % n.z);
-    const int64_t rest = e / n.z;
-    const int gy = int(rest % n.y), gz = int(rest / n.y);
-    const int64_t yo = fmap(gz, s.x, N.x) * y_sz + fmap(gy, s.y, N.y) * y_sy + fmap(gx, s.z, N.z);
-    if (dir == 0) w[e] = TW(y[yo]);
-    else y[yo] = TD(w[e]);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Host-side level loops
 // ---------------------------------------------------------------------------
 
@@ -288,20 +124,6 @@ inline Bufs split_ws(const mgr_plan* p, void* ws) {
   return Bufs{b, b + p->ws_a, b + p->ws_a + p->ws_b};
 }
 
-// Tile configuration of the level pass per stencil type: 8 warps with two
-// row pairs each (two CTAs per SM); FP64 uses a single cp.async stage (the
-// FP64 pipe, not memory latency, bounds it, and the smaller footprint keeps
-// two CTAs per SM), FP32 two stages.
-template <typename TS>
-struct LevelCfg;
-template <>
-struct LevelCfg<double> {
-  static constexpr int NW = 8, RPW = 2, STAGES = 1;
-};
-template <>
-struct LevelCfg<float> {
-  static constexpr int NW = 8, RPW = 2, STAGES = 2;
-};
 constexpr int kInterpNW = 8, kInterpRPW = 2;
 
 template <typename TS, typename TW>
@@ -421,35 +243,24 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   const TW* T = table<TW>(p);
   const TW* ta = T + g.ax[axis].o_ta;
   const TW* tb = T + g.ax[axis].o_tb;
+  const int64_t lines_x = int64_t(mz) * my;
   if (axis == 2 && sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
     // lines too long to stage in shared memory: one thread per line from global memory
-    const int64_t rows = int64_t(mz) * my;
     const int threads = 128;
-    const int blocks = int((rows + threads - 1) / threads);
-    if (op == SOLVE_INPLACE)
-      k_solve_strided<TW, SOLVE_INPLACE><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
-    else if (op == SOLVE_ADD)
-      k_solve_strided<TW, SOLVE_ADD><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
-    else
-      k_solve_strided<TW, SOLVE_SUB><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, rows, mx, ta, tb);
+    const int blocks = int((lines_x + threads - 1) / threads);
+    k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, lines_x, mx, ta, tb, op);
     return cudaGetLastError();
   }
   if (axis == 2) {
-    const int64_t rows = int64_t(mz) * my;
     const int pitch = mx | 1;
     // rows per CTA (one solving thread per row, 128 threads load and store):
     // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
     int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
     R = std::max(1, R);
     const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
-    const int blocks = int((rows + R - 1) / R);
-    auto launch = [&](auto kern) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-      kern<<<blocks, 128, sm, st>>>(f, w, mx, rows, mx, R, ta, tb);
-    };
-    if (op == SOLVE_INPLACE) launch(k_solve_contig<TW, SOLVE_INPLACE>);
-    else if (op == SOLVE_ADD) launch(k_solve_contig<TW, SOLVE_ADD>);
-    else launch(k_solve_contig<TW, SOLVE_SUB>);
+    const int blocks = int((lines_x + R - 1) / R);
+    cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines_x, mx, R, ta, tb, op);
     return cudaGetLastError();
   }
   int mline, inner;
@@ -462,12 +273,7 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   const int64_t lines = int64_t(inner) * outer;
   const int threads = 128;
   const int blocks = int((lines + threads - 1) / threads);
-  if (op == SOLVE_INPLACE)
-    k_solve_strided<TW, SOLVE_INPLACE><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb);
-  else if (op == SOLVE_ADD)
-    k_solve_strided<TW, SOLVE_ADD><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb);
-  else
-    k_solve_strided<TW, SOLVE_SUB><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb);
+  k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb, op);
   return cudaGetLastError();
 }
 

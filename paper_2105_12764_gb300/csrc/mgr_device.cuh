@@ -1,0 +1,35 @@
+// mgr_device.cuh -- small device helpers shared by the kernels of this
+// library (index maps of the nested hierarchy and cp.async wrappers).
+// Included inside an anonymous namespace of each translation unit.
+#pragma once
+
+__device__ __forceinline__ int pidx(int q, int n) { return min(2 * q, n - 1); }
+__device__ __forceinline__ bool is_coarse(int i, int n) { return ((i & 1) == 0) || (i == n - 1); }
+__device__ __forceinline__ int cidx(int i) { return (i + 1) >> 1; }
+// first fine node of the stencil region of coarse node q0, moved down to a coarse node
+__device__ __forceinline__ int region_start(int q0, int n) {
+  const int r = pidx(q0, n) - 2;
+  return (r & 1) ? r - 1 : r;
+}
+__device__ __forceinline__ int64_t fmap(int i, int64_t s, int64_t N) {
+  int64_t f = int64_t(i) * s;
+  return f < N - 1 ? f : N - 1;
+}
+
+// Asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses
+// aligned to the copy size).
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+

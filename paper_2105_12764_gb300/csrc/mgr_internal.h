@@ -120,6 +120,12 @@ Work work_interp(const mgr_plan* p, int l);
 int build_plan_tables(mgr_plan* p);
 int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels);
 
+// mgr_batch.cu: batched refactoring (context-owned state in mgr_ctx::batch).
+int batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket);
+int batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_done);
+int batch_tuning(mgr_ctx* ctx, char* buf, size_t len);
+void batch_destroy(mgr_ctx* ctx);
+
 // mgr_core.cu: enqueue one whole operation (all levels) on `st` (no graph).
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);

@@ -39,6 +39,20 @@ struct LevelTile {
   static constexpr int CP = RC + 2;        // c row pitch: even, so column pairs stay 8/16-byte aligned
 };
 
+// Tile configuration of the level pass per stencil type: 8 warps with two
+// row pairs each (two CTAs per SM); FP64 uses a single cp.async stage (the
+// FP64 pipe, not memory latency, bounds it, and the smaller footprint keeps
+// two CTAs per SM), FP32 two stages.
+template <typename TS>
+struct LevelCfg;
+template <>
+struct LevelCfg<double> {
+  static constexpr int NW = 8, RPW = 2, STAGES = 1;
+};
+template <>
+struct LevelCfg<float> {
+  static constexpr int NW = 8, RPW = 2, STAGES = 2;
+};
 template <typename T>
 struct Pair;
 template <>
@@ -104,14 +118,16 @@ __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bo
   }
 }
 
+// One CTA's work: coarse tile (bx, by) and z chunk bz of level args `a`,
+// with `smem_raw` the CTA's dynamic shared memory (level_smem_bytes).
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
+__device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, int by, int bz,
+                                           unsigned char* smem_raw) {
   using G = LevelTile<NW, RPW>;
   using TS2 = typename Pair<TS>::type;
   using TI2 = typename Pair<TI>::type;
   constexpr int RR = G::RR, RC = G::RC, CP = G::CP;
   constexpr unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TI* stage = reinterpret_cast<TI*>(smem_raw);                                       // [STAGES][2][RR][RC]
   TS* cbuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * STAGES * 2 * RR * RC);  // [2][RR][CP]
   TS* xch = cbuf + 2 * RR * CP;                                                     // [NW][RC]
@@ -120,9 +136,9 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
   const int mz = a.m[0], my = a.m[1], mx = a.m[2];
-  const int qx0 = blockIdx.x * G::BX, qx1 = min(qx0 + G::BX, mx);
-  const int qy0 = blockIdx.y * G::BY, qy1 = min(qy0 + G::BY, my);
-  const int qz0 = blockIdx.z * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
+  const int qx0 = bx * G::BX, qx1 = min(qx0 + G::BX, mx);
+  const int qy0 = by * G::BY, qy1 = min(qy0 + G::BY, my);
+  const int qz0 = bz * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
   const int rx0 = max(region_start(qx0, nx), 0), rx1 = min(pidx(qx1 - 1, nx) + 2, nx - 1);
   const int ry0 = max(region_start(qy0, ny), 0), ry1 = min(pidx(qy1 - 1, ny) + 2, ny - 1);
   const int ox0 = pidx(qx0, nx), ox1 = (qx1 == mx) ? nx : pidx(qx1, nx);
@@ -484,6 +500,12 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a)
   }
 }
 
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Recomposition interpolation (Sec. II.A, recomposition): level-l values
 // v = c + (P_z x P_y x P_x) v_coarse.  A CTA owns 32 x (NW*RPW) coarse
@@ -516,17 +538,17 @@ constexpr size_t interp_smem_bytes() {
 }
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
+__device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx, int by, int bz,
+                                            unsigned char* smem_raw) {
   constexpr int BY = NW * RPW, TR = BY + 1, TC = 33, RR = 2 * BY, RC = 64;
   using TD2 = typename Pair<TD>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   TD* stage = reinterpret_cast<TD*>(smem_raw);                                  // [2][2][RR][RC]
   TW* tile = reinterpret_cast<TW*>(smem_raw + sizeof(TD) * 2 * 2 * RR * RC);  // [2][TR][TC]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
   const int mz = a.m[0], my = a.m[1], mx = a.m[2];
-  const int qx0 = blockIdx.x * 32, qy0 = blockIdx.y * BY;
-  const int qz0 = blockIdx.z * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
+  const int qx0 = bx * 32, qy0 = by * BY;
+  const int qz0 = bz * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
   const int t_end = min(qz1, mz - 1);
   const int tcols = min(TC, mx - qx0), trows = min(TR, my - qy0);
   const TD* __restrict__ cin = static_cast<const TD*>(a.c);
@@ -660,4 +682,10 @@ __global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> 
     }
     __syncthreads();  // both stage buffers are reloaded two iterations later
   }
+}
+
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+__global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  interp_body<NW, RPW, TD, TO, TS, TW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }

@@ -1,0 +1,176 @@
+// mgr_solve.cuh -- Thomas solves of the coarse mass matrix along one axis
+// (arXiv 2105.12764, Sec. III.A.3) and the coarsest-grid copy, as per-CTA
+// bodies (used by the single-field kernels below and by the batched ones).
+//
+// The LU of the coarse mass matrix is scaled so each step is one FMA (the
+// diagonal 1/u_q is folded into the mass-transfer stencil):
+//   forward   y_q = f'_q - ta_q * y_{q-1}
+//   backward  z_q = y_q  - tb_q * z_{q+1}
+// The last axis of a level applies the correction (Eq. (1)) into the coarse
+// workspace: w += z (decompose) or w -= z (recompose).
+#pragma once
+
+enum { SOLVE_INPLACE = 0, SOLVE_ADD = 1, SOLVE_SUB = 2 };
+
+template <typename TW>
+__device__ __forceinline__ void apply_op(TW* f, TW* w, int64_t g, TW v, int op) {
+  if (op == SOLVE_INPLACE) f[g] = v;
+  else if (op == SOLVE_ADD) w[g] = w[g] + v;
+  else w[g] = w[g] - v;
+}
+
+// Lines along a strided axis, one thread per line: element q of line
+// (o, i) sits at o*ostride + i + q*lstride; consecutive threads take
+// consecutive i, so every step is a coalesced access.  `line` is this
+// thread's line index in [0, inner*outer).
+template <typename TW>
+__device__ __forceinline__ void solve_strided_line(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t lstride,
+                                                   int inner, int64_t ostride, const TW* __restrict__ ta,
+                                                   const TW* __restrict__ tb, int op, int64_t line) {
+  const int i = int(line % inner);
+  const int64_t o = line / inner;
+  TW* fl = f + o * ostride + i;
+  constexpr int U = 8;
+  TW prev = TW(0);
+  for (int q0 = 0; q0 < mline; q0 += U) {
+    TW buf[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q0 + u < mline) buf[u] = fl[int64_t(q0 + u) * lstride];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q0 + u < mline) {
+        prev = buf[u] - ta[q0 + u] * prev;
+        fl[int64_t(q0 + u) * lstride] = prev;
+      }
+  }
+  TW* wl = w + o * ostride + i;
+  TW next = TW(0);
+  for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
+    TW buf[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q1 - u >= 0) buf[u] = fl[int64_t(q1 - u) * lstride];
+    TW wv[U];
+    if (op != SOLVE_INPLACE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q1 - u >= 0) wv[u] = wl[int64_t(q1 - u) * lstride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q1 - u >= 0) {
+        const int q = q1 - u;
+        next = buf[u] - tb[q] * next;
+        if (op == SOLVE_INPLACE) fl[int64_t(q) * lstride] = next;
+        else if (op == SOLVE_ADD) wl[int64_t(q) * lstride] = wv[u] + next;
+        else wl[int64_t(q) * lstride] = wv[u] - next;
+      }
+  }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* __restrict__ w, int mline,
+                                                       int64_t lstride, int inner, int64_t outer, int64_t ostride,
+                                                       const TW* __restrict__ ta, const TW* __restrict__ tb, int op) {
+  const int64_t id = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (id >= int64_t(inner) * outer) return;
+  solve_strided_line<TW>(f, w, mline, lstride, inner, ostride, ta, tb, op, id);
+}
+
+// Lines along the contiguous axis: R rows of length mline (row pitch
+// row_pitch) starting at row r0 are staged in shared memory with coalesced
+// loads/stores by all threads; thread r < R then runs its row's recurrences
+// in register chunks of 8 (eight independent loads, eight dependent FMAs,
+// eight stores).  The recurrence coefficients are staged once.
+template <typename TW>
+__device__ __forceinline__ size_t solve_contig_smem(int mline, int R) {
+  return sizeof(TW) * (size_t(R) * (mline | 1) + 2 * size_t(mline));
+}
+
+template <typename TW>
+__device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows,
+                                                  int64_t row_pitch, int R, const TW* __restrict__ ta,
+                                                  const TW* __restrict__ tb, int op, int64_t r0,
+                                                  unsigned char* smem_raw) {
+  const int pitch = mline | 1;  // odd pitch spreads the rows of a warp over the banks
+  TW* s = reinterpret_cast<TW*>(smem_raw);  // [R][pitch]
+  TW* sa = s + R * pitch;                   // [mline]
+  TW* sb = sa + mline;                      // [mline]
+  const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
+  for (int q = threadIdx.x; q < mline; q += blockDim.x) {
+    sa[q] = ta[q];
+    sb[q] = tb[q];
+  }
+  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
+    const int r = e / mline, c = e - r * mline;
+    s[r * pitch + c] = f[(r0 + r) * row_pitch + c];
+  }
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    TW* l = s + threadIdx.x * pitch;
+    constexpr int U = 8;
+    TW prev = TW(0);
+    for (int q0 = 0; q0 < mline; q0 += U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q0 + u < mline) ? l[q0 + u] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        prev = v[u] - sa[min(q0 + u, mline - 1)] * prev;
+        v[u] = prev;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q0 + u < mline) l[q0 + u] = v[u];
+    }
+    TW next = TW(0);
+    for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q1 - u >= 0) ? l[q1 - u] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        next = v[u] - sb[max(q1 - u, 0)] * next;
+        v[u] = next;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q1 - u >= 0) l[q1 - u] = v[u];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
+    const int r = e / mline, c = e - r * mline;
+    apply_op<TW>(f, w, (r0 + r) * row_pitch + c, s[r * pitch + c], op);
+  }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_solve_contig(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows,
+                                                      int64_t row_pitch, int R, const TW* __restrict__ ta,
+                                                      const TW* __restrict__ tb, int op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  solve_contig_rows<TW>(f, w, mline, rows, row_pitch, R, ta, tb, op, blockIdx.x * int64_t(R), smem_raw);
+}
+
+// Coarsest grid <-> nodal positions (dir 0: gather nodal -> compact; 1: scatter)
+template <typename TD, typename TW>
+__device__ __forceinline__ void coarsest_copy(TD* y, int64_t y_sz, int64_t y_sy, TW* w, int3 n, longlong3 s,
+                                              longlong3 N, int dir, int64_t e0, int64_t estep) {
+  const int64_t total = int64_t(n.x) * n.y * n.z;
+  for (int64_t e = e0; e < total; e += estep) {
+    const int gx = int(e % n.z);
+    const int64_t rest = e / n.z;
+    const int gy = int(rest % n.y), gz = int(rest / n.y);
+    const int64_t yo = fmap(gz, s.x, N.x) * y_sz + fmap(gy, s.y, N.y) * y_sy + fmap(gx, s.z, N.z);
+    if (dir == 0) w[e] = TW(y[yo]);
+    else y[yo] = TD(w[e]);
+  }
+}
+
+template <typename TD, typename TW>
+__global__ void k_coarsest(TD* y, int64_t y_sz, int64_t y_sy, TW* w, int3 n, longlong3 s, longlong3 N, int dir) {
+  coarsest_copy<TD, TW>(y, y_sz, y_sy, w, n, s, N, dir, blockIdx.x * int64_t(blockDim.x) + threadIdx.x,
+                        int64_t(gridDim.x) * blockDim.x);
+}
