@@ -183,6 +183,60 @@ int mgr_batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_don
    terminating NUL; returns the full length. */
 int mgr_batch_tuning(mgr_ctx* ctx, char* buf, size_t len);
 
+/* ------------------------------------------------------------ serving */
+
+/* The serving pattern: a request loop that admits decompose / recompose
+   requests of mixed sizes by device-memory budget and keeps hierarchies
+   resident.  Requests enter a FIFO queue; a dispatcher admits the head as
+   soon as one of `slots` execution slots is free and its device memory (its
+   workspace, plus the hierarchy for a decomposition) fits the context's
+   budget, evicting least recently used resident hierarchies that no request
+   references.  Admitted requests run on a pool of `streams` streams, so work
+   of requests that arrive while others run overlaps on the device
+   (continuous batching).  A decomposition writes its hierarchy (nodal
+   coefficients) into library memory; with keep_resident it stays resident
+   under a handle equal to the request id, for later recompositions. */
+typedef struct mgr_server mgr_server;
+
+typedef struct {
+  int op;               /* MGR_OP_DECOMPOSE: in -> resident hierarchy;
+                           MGR_OP_RECOMPOSE: resident hierarchy `src` -> out */
+  const mgr_plan* plan; /* field description (the plan must outlive the request) */
+  const void* in;       /* decompose: DEVICE field, read while the request runs */
+  uint64_t src;         /* recompose: handle of a finished resident hierarchy  */
+  void* out;            /* recompose: DEVICE field buffer                      */
+  int keep_resident;    /* decompose: keep the hierarchy after completion      */
+  double arrival;       /* arrival time (mgr_serve_now() clock); 0 = now       */
+} mgr_serve_request;
+
+typedef struct {
+  int status;      /* MGR_OK, or the request's error (MGR_EBUDGET, MGR_ECUDA, ...) */
+  double arrival;  /* seconds, mgr_serve_now() clock                               */
+  double admitted; /* when it was launched                                        */
+  double done;     /* when its completion was observed                             */
+  uint64_t handle; /* resident hierarchy handle (decompose with keep_resident)     */
+} mgr_serve_result;
+
+/* Steady clock in seconds used for the request time stamps. */
+double mgr_serve_now(void);
+int mgr_serve_start(mgr_ctx* ctx, int slots, int streams, mgr_server** server);
+/* Queue a request.  MGR_EBUDGET if it can never fit the budget, MGR_ENOTFOUND
+   for an unknown hierarchy, MGR_EPENDING if that hierarchy is not finished. */
+int mgr_serve_enqueue(mgr_server* server, const mgr_serve_request* req, uint64_t* id);
+/* Wait up to timeout_us (0: poll, < 0: no limit) for request `id`; on MGR_OK
+   fills *res and forgets the request.  MGR_EPENDING / MGR_ETIMEDOUT otherwise. */
+int mgr_serve_wait(mgr_server* server, uint64_t id, int64_t timeout_us, mgr_serve_result* res);
+/* Device pointer of a finished resident hierarchy (nodal layout of its plan). */
+int mgr_serve_hierarchy(mgr_server* server, uint64_t handle, const void** ptr);
+/* Copy a finished resident hierarchy into the caller's DEVICE buffer `dst`
+   (field-sized) on `stream`. */
+int mgr_serve_read(mgr_server* server, uint64_t handle, void* dst, mgr_stream_t stream);
+/* Drop a resident hierarchy (MGR_EPENDING while a request still uses it). */
+int mgr_serve_release(mgr_server* server, uint64_t handle);
+int mgr_serve_stats(mgr_server* server, size_t* used_bytes, int* queued, int* running, int* resident);
+/* Finish all queued and running requests, free every resident hierarchy. */
+int mgr_serve_stop(mgr_server* server);
+
 /* ------------------------------------------------------------ profiling */
 
 /* One kernel launch of an operation, timed by CUDA events recorded on the

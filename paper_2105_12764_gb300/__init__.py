@@ -15,7 +15,7 @@ import os
 __all__ = [
     "MGR_OK", "MGR_EINVAL", "MGR_ENOMEM", "MGR_EBUDGET", "MGR_ECUDA", "MGR_EPENDING", "MGR_ETIMEDOUT",
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
-    "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE", "lib", "library_path", "Context", "Plan", "EXPORTED",
+    "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE", "Server", "lib", "library_path", "Context", "Plan", "EXPORTED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +67,28 @@ class mgr_request(ctypes.Structure):
 
 MGR_OP_DECOMPOSE, MGR_OP_RECOMPOSE = 0, 1
 
+
+class mgr_serve_request(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int),
+        ("plan", ctypes.c_void_p),
+        ("in_", ctypes.c_void_p),
+        ("src", ctypes.c_uint64),
+        ("out", ctypes.c_void_p),
+        ("keep_resident", ctypes.c_int),
+        ("arrival", ctypes.c_double),
+    ]
+
+
+class mgr_serve_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("arrival", ctypes.c_double),
+        ("admitted", ctypes.c_double),
+        ("done", ctypes.c_double),
+        ("handle", ctypes.c_uint64),
+    ]
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 # name -> (restype, argtypes): every entry point declared in include/mgr.h
@@ -89,6 +111,16 @@ EXPORTED = {
     "mgr_batch_submit": (_i, [_vp, ctypes.POINTER(mgr_request), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mgr_batch_poll": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_i)]),
     "mgr_batch_tuning": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
+    "mgr_serve_now": (ctypes.c_double, []),
+    "mgr_serve_start": (_i, [_vp, _i, _i, ctypes.POINTER(_vp)]),
+    "mgr_serve_enqueue": (_i, [_vp, ctypes.POINTER(mgr_serve_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "mgr_serve_wait": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(mgr_serve_result)]),
+    "mgr_serve_hierarchy": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "mgr_serve_read": (_i, [_vp, ctypes.c_uint64, _vp, _vp]),
+    "mgr_serve_release": (_i, [_vp, ctypes.c_uint64]),
+    "mgr_serve_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                             ctypes.POINTER(_i)]),
+    "mgr_serve_stop": (_i, [_vp]),
 }
 
 
@@ -276,3 +308,64 @@ def default_levels(shape):
     v = _i()
     _check("mgr_default_levels", lib.mgr_default_levels(ctypes.byref(d), ctypes.byref(v)))
     return v.value
+
+
+class Server:
+    """mgr_serve_*: continuous-batching request loop on one context."""
+
+    def __init__(self, ctx, slots=4, streams=4):
+        h = _vp()
+        _check("mgr_serve_start", lib.mgr_serve_start(ctx.handle, int(slots), int(streams), ctypes.byref(h)))
+        self.handle = h.value
+        self.ctx = ctx
+
+    @staticmethod
+    def now():
+        return lib.mgr_serve_now()
+
+    def enqueue(self, op, plan, inp=None, src=0, out=None, keep_resident=1, arrival=0.0):
+        r = mgr_serve_request()
+        r.op = int(op)
+        r.plan = plan.handle
+        r.in_ = _ptr(inp)
+        r.src = int(src)
+        r.out = _ptr(out)
+        r.keep_resident = int(keep_resident)
+        r.arrival = float(arrival)
+        i = ctypes.c_uint64()
+        _check("mgr_serve_enqueue", lib.mgr_serve_enqueue(self.handle, ctypes.byref(r), ctypes.byref(i)))
+        return i.value
+
+    def wait(self, rid, timeout_us=-1):
+        """Returns (code, result dict or None)."""
+        res = mgr_serve_result()
+        rc = lib.mgr_serve_wait(self.handle, int(rid), int(timeout_us), ctypes.byref(res))
+        if rc in (MGR_EPENDING, MGR_ETIMEDOUT):
+            return rc, None
+        _check("mgr_serve_wait", rc)
+        return rc, dict(status=res.status, arrival=res.arrival, admitted=res.admitted, done=res.done,
+                        handle=res.handle)
+
+    def hierarchy(self, handle):
+        p = _vp()
+        _check("mgr_serve_hierarchy", lib.mgr_serve_hierarchy(self.handle, int(handle), ctypes.byref(p)))
+        return p.value
+
+    def read(self, handle, dst, stream=None):
+        """mgr_serve_read: copy a finished resident hierarchy into device buffer `dst`."""
+        _check("mgr_serve_read", lib.mgr_serve_read(self.handle, int(handle), _ptr(dst), _stream(stream)))
+
+    def release(self, handle):
+        return lib.mgr_serve_release(self.handle, int(handle))
+
+    def stats(self):
+        u, q, r, h = ctypes.c_size_t(), _i(), _i(), _i()
+        _check("mgr_serve_stats", lib.mgr_serve_stats(self.handle, ctypes.byref(u), ctypes.byref(q), ctypes.byref(r),
+                                                      ctypes.byref(h)))
+        return dict(used_bytes=u.value, queued=q.value, running=r.value, resident=h.value)
+
+    def stop(self):
+        if self.handle:
+            _check("mgr_serve_stop", lib.mgr_serve_stop(self.handle))
+            self.handle = None
+

@@ -145,3 +145,57 @@ def workload(name, seed=0, shape=None):
         return grf_field(shape, seed), None
     coords = [stretched_coords(n) for n in shape]
     return bumps_field(shape, seed, coords=coords), coords
+
+
+# ---------------------------------------------------------------------------
+# C4: thousands of uneven fields for the batched form
+# ---------------------------------------------------------------------------
+
+def c4_field_specs(count=4096, seed=0):
+    """(shape, stretched) of the batched workload.
+
+    Element count N is log-uniform on [17^2, 129^3]; N <= 129^2 gives a
+    near-square 2D field, larger N a near-cube 3D field; every side is in
+    [17, 129] and not forced to 2^k+1; half the fields (p = 1/2) use
+    geometric coordinates with ratio 1.01 per cell, the others unit spacing.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(17.0 ** 2), np.log(129.0 ** 3)
+    specs = []
+    for _ in range(count):
+        n = float(np.exp(rng.uniform(lo, hi)))
+        if n <= 129.0 ** 2:
+            a = int(np.clip(round(np.sqrt(n) * rng.uniform(0.85, 1.15)), 17, 129))
+            b = int(np.clip(round(n / a), 17, 129))
+            shape = (a, b)
+        else:
+            a = int(np.clip(round(n ** (1.0 / 3.0) * rng.uniform(0.85, 1.15)), 17, 129))
+            b = int(np.clip(round((n / a) ** 0.5 * rng.uniform(0.9, 1.1)), 17, 129))
+            c = int(np.clip(round(n / (a * b)), 17, 129))
+            shape = (a, b, c)
+        specs.append((shape, bool(rng.random() < 0.5)))
+    return specs
+
+
+def grf_field_torch(shape, seed=0, slope=-5.0 / 3.0, device="cuda"):
+    """Gaussian random field with power |k|^slope, generated with torch on
+    `device` from a seeded generator (same recipe as grf_field); FP64 result,
+    mean 0 and variance 1."""
+    import torch
+
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    white = torch.randn(tuple(shape), generator=g, device=device, dtype=torch.float64)
+    spec = torch.fft.rfftn(white)
+    d = len(shape)
+    k2 = None
+    for ax in range(d):
+        n = shape[ax]
+        k = (torch.fft.rfftfreq(n, device=device) if ax == d - 1 else torch.fft.fftfreq(n, device=device)) * n
+        sh = [1] * d
+        sh[ax] = k.shape[0]
+        term = k.reshape(sh).to(torch.float64) ** 2
+        k2 = term if k2 is None else k2 + term
+    amp = torch.where(k2 > 0, k2.clamp_min(1e-300) ** (slope / 4.0), torch.zeros_like(k2))
+    u = torch.fft.irfftn(spec * amp, s=tuple(shape))
+    u = u - u.mean()
+    return u / u.std()
