@@ -140,6 +140,33 @@ int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out
 int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
                        void* workspace, mgr_stream_t stream);
 
+/* ------------------------------------------------------------ no-alloc form */
+
+/* Size of the fixed device scratch area used by mgr_decompose_noalloc. */
+#define MGR_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Decomposition for callers that cannot allocate device memory (their
+   device memory is entirely owned by another allocator, they are handed
+   only their input and output buffers, or an allocation -- which may
+   synchronise the device -- is not acceptable on their path).  The paper
+   has no counterpart: this is a calling convention of this library.
+   Same operation and arguments as mgr_decompose, without the workspace:
+   the workspace is a fixed MGR_NOALLOC_SCRATCH_BYTES area in this library's
+   device image, which every GPU that loads the library holds until the
+   process exits.  The call allocates nothing (no cudaMalloc / cudaFree) and
+   launches the kernels directly on `stream`.
+     - Returns MGR_EINVAL when the plan's mgr_workspace_size() exceeds
+       MGR_NOALLOC_SCRATCH_BYTES (for example FP64 fields of more than about
+       15 million nodes), and for the argument errors of mgr_decompose.
+     - The first call on a device looks up the area's device address (with
+       that device made current for the lookup); make that first call before
+       any stream capture.
+     - Every call on a device shares the one area, which keeps the previous
+       call's contents (nothing in it needs to start at zero).  Calls whose
+       work overlaps on the GPU (different streams, or other host threads)
+       race on it: serialise them. */
+int mgr_decompose_noalloc(const mgr_plan* plan, const void* in, void* out, mgr_stream_t stream);
+
 /* ------------------------------------------------------------ batching */
 
 #define MGR_OP_DECOMPOSE 0

@@ -25,6 +25,7 @@ MGR_OK, MGR_EINVAL, MGR_ENOMEM, MGR_EBUDGET, MGR_ECUDA = 0, -1, -2, -3, -4
 MGR_EPENDING, MGR_ETIMEDOUT, MGR_EDEVICE, MGR_ENOTFOUND, MGR_EBUSY = -5, -6, -7, -8, -9
 MGR_F32, MGR_F64 = 0, 1
 MGR_PREC_NATIVE, MGR_PREC_MIXED = 0, 1
+MGR_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class MgrError(RuntimeError):
@@ -108,6 +109,7 @@ EXPORTED = {
     "mgr_decompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
+    "mgr_decompose_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mgr_batch_submit": (_i, [_vp, ctypes.POINTER(mgr_request), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mgr_batch_poll": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_i)]),
     "mgr_batch_tuning": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -266,6 +268,11 @@ class Plan:
 
     def recompose(self, inp, out, workspace, stream=None):
         _check("mgr_recompose", lib.mgr_recompose(self.handle, _ptr(inp), _ptr(out), _ptr(workspace), _stream(stream)))
+
+    def decompose_noalloc(self, inp, out, stream=None):
+        """mgr_decompose_noalloc: no workspace argument, no device allocation (fields whose workspace
+        fits MGR_NOALLOC_SCRATCH_BYTES; calls that overlap on the GPU must be serialised)."""
+        _check("mgr_decompose_noalloc", lib.mgr_decompose_noalloc(self.handle, _ptr(inp), _ptr(out), _stream(stream)))
 
     def decompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
         _check("mgr_decompose_host", lib.mgr_decompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),
