@@ -1,0 +1,82 @@
+"""Per-kernel timing of one decomposition + recomposition.
+
+    python -m paper_2105_12764_gb300.profile --form fp64 --shape 513 [--reps 3]
+
+prints every kernel role (level pass, solves, interpolation, ...) with its
+CUDA-event time and the achieved bandwidth / flop rate of its algorithmic
+work (mgr_profile), then the graph-replayed decompose and recompose times.
+With --plain it only runs the operations (no event brackets): a clean target
+for an external profiler.
+"""
+import argparse
+import os
+import sys
+
+sys.path.append(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    import torch
+
+    import paper_2105_12764_gb300 as mgr
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--form", choices=["fp64", "fp32", "mixed"], default="fp64")
+    ap.add_argument("--shape", default="513", help="n (cube) or n0,n1,n2")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--plain", action="store_true")
+    a = ap.parse_args()
+    shape = tuple(int(v) for v in a.shape.split(","))
+    if len(shape) == 1:
+        shape = shape * 3
+    dtype = mgr.MGR_F64 if a.form == "fp64" else mgr.MGR_F32
+    prec = mgr.MGR_PREC_MIXED if a.form == "mixed" else mgr.MGR_PREC_NATIVE
+    td = torch.float64 if dtype == mgr.MGR_F64 else torch.float32
+    ctx = mgr.Context(0)
+    plan = mgr.Plan(ctx, shape, None, -1, dtype, prec)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(shape, dtype=td, device="cuda", generator=g)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    if a.plain:
+        for _ in range(a.reps):
+            plan.decompose(x, y, ws)
+            plan.recompose(y, z, ws)
+        torch.cuda.synchronize()
+        print(f"done: round trip max error {float((z - x).abs().max()):.3e}")
+        return
+    for _ in range(2):
+        plan.decompose(x, y, ws)
+        plan.recompose(y, z, ws)
+    torch.cuda.synchronize()
+    agg = {}
+    for _ in range(a.reps):
+        for op, (src, dst) in ((0, (x, y)), (1, (y, z))):
+            for r in plan.profile(op, src, dst, ws):
+                e = agg.setdefault((r["name"], r["level"]), [0.0, 0, r["bytes"], r["flops"]])
+                e[0] += r["ms"]
+                e[1] += 1
+    tot = sum(v[0] / v[1] for v in agg.values())
+    print(f"form {a.form} shape {shape} levels {plan.levels}: {tot:.3f} ms per decompose + recompose "
+          f"(sum of event-bracketed launches)")
+    for (name, lvl), v in sorted(agg.items(), key=lambda kv: -kv[1][0])[:24]:
+        ms = v[0] / v[1]
+        print(f"  {name:16s} L{lvl:<2d} {ms:8.4f} ms {v[2] / ms / 1e6:9.1f} GB/s {v[3] / ms / 1e9:7.3f} TFLOP/s "
+              f"share {ms / tot:.3f}")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(a.reps):
+        plan.decompose(x, y, ws)
+    ev[1].record()
+    for _ in range(a.reps):
+        plan.recompose(y, z, ws)
+    ev[2].record()
+    torch.cuda.synchronize()
+    print(f"graph-replayed: decompose {ev[0].elapsed_time(ev[1]) / a.reps:.3f} ms, "
+          f"recompose {ev[1].elapsed_time(ev[2]) / a.reps:.3f} ms")
+    plan.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
