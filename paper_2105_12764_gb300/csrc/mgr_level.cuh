@@ -83,11 +83,19 @@ struct LevelArgs {
   int write_y;
 };
 
+// FP64 keeps the x / y stencil weights in shared memory (the FP64 pass is
+// bound by the FP64 pipe and short of registers), FP32 in registers (its
+// pass is bound by instruction issue).
+template <typename TS>
+constexpr bool weights_in_smem() {
+  return sizeof(TS) == 8;
+}
+
 template <int NW, int RPW, int STAGES, typename TI, typename TS>
 constexpr size_t level_smem_bytes() {
   using G = LevelTile<NW, RPW>;
   return sizeof(TI) * STAGES * 2 * G::RR * G::RC +
-         sizeof(TS) * (2 * G::RR * G::CP + NW * G::RC + 2 * G::RR * 32);
+         sizeof(TS) * (2 * G::RR * G::CP + NW * G::RC + 2 * G::RR * 32 + 5 * 32 + 5 * NW * RPW);
 }
 
 // Copy the element pair (c0, c0+1) of one row into shared memory: one
@@ -132,6 +140,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   TS* cbuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * STAGES * 2 * RR * RC);  // [2][RR][CP]
   TS* xch = cbuf + 2 * RR * CP;                                                     // [NW][RC]
   TS* gxb = xch + NW * RC;                                                          // [2][RR][32]
+  TS* kxs = gxb + 2 * RR * 32;                                                      // [5][32]
+  TS* kys = kxs + 5 * 32;                                                           // [5][NW*RPW]
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
@@ -170,14 +180,23 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const int qxo = min(qx0 + lane, mx - 1);
   const int px = pidx(qxo, nx);
   const int dx = px - rx0;  // slot of the stencil centre
-  TS kx[5];
+  TS kxr[weights_in_smem<TS>() ? 1 : 5];
   unsigned kxm = 0;  // taps inside the grid
 #pragma unroll
   for (int o = 0; o < 5; ++o) {
-    kx[o] = a.k[2][5 * qxo + o];
+    const TS kw = a.k[2][5 * qxo + o];
+    if constexpr (weights_in_smem<TS>()) {
+      if (warp == 0) kxs[o * 32 + lane] = kw;
+    } else {
+      kxr[o] = kw;
+    }
     const int j = px + o - 2;
     if (j >= 0 && j < nx) kxm |= 1u << o;
   }
+  auto kx = [&](int o) -> TS {
+    if constexpr (weights_in_smem<TS>()) return kxs[o * 32 + lane];
+    else return kxr[o];
+  };
   // interior column: taps px +- 1 fine, px and px +- 2 coarse, even slot
   const bool kx_generic = kxm == 31u && (px & 1) == 0 && px + 1 < nx - 1;
 
@@ -188,7 +207,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   int ir0[RPW], ir1[RPW], yr0[RPW], yr1[RPW];
   // y stencil of this thread's output rows
   const int nby = qy1 - qy0;
-  TS ky[RPW][5];
+  TS kyr[RPW][weights_in_smem<TS>() ? 1 : 5];
   unsigned kym[RPW];
   int dyo[RPW];
 #pragma unroll
@@ -213,11 +232,21 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     kym[k] = 0;
 #pragma unroll
     for (int o = 0; o < 5; ++o) {
-      ky[k][o] = a.k[1][5 * qy + o];
+      const TS kw = a.k[1][5 * qy + o];
+      if constexpr (weights_in_smem<TS>()) {
+        if (lane == 0) kys[o * (NW * RPW) + warp * RPW + k] = kw;
+      } else {
+        kyr[k][o] = kw;
+      }
       const int jj = py + o - 2;
       if (jj >= 0 && jj < ny) kym[k] |= 1u << o;
     }
   }
+  auto ky = [&](int k, int o) -> TS {
+    if constexpr (weights_in_smem<TS>()) return kys[o * (NW * RPW) + warp * RPW + k];
+    else return kyr[k][o];
+  };
+  __syncthreads();  // stencil weights staged
 
   auto iplane = [&](int g) -> int64_t {
     return a.in_full ? fmap(g, a.s[0], a.N[0]) * a.in_sz : int64_t(g) * a.in_sz;
@@ -276,7 +305,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     const bool own_f = hf && (t > qz0) && (t <= qz1);
 
     // ---- this thread's values of both planes (pairs from shared memory)
-    TS vc[RPW][4], vf[RPW][4];
+    TS vc[RPW][4];
     TI rc[RPW][4];  // raw coarse-plane values: exact copies for the coarse workspace
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
@@ -289,16 +318,6 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       rc[k][3] = p1.y;
 #pragma unroll
       for (int e = 0; e < 4; ++e) vc[k][e] = TS(rc[k][e]);
-      if (hf) {
-        const TI2 f0 = *reinterpret_cast<const TI2*>(sf + r0 * RC + cx0);
-        const TI2 f1 = *reinterpret_cast<const TI2*>(sf + (r0 + 1) * RC + cx0);
-        vf[k][0] = TS(f0.x);
-        vf[k][1] = TS(f0.y);
-        vf[k][2] = TS(f1.x);
-        vf[k][3] = TS(f1.y);
-      } else {
-        vf[k][0] = vf[k][1] = vf[k][2] = vf[k][3] = TS(0);
-      }
     }
     // ---- coarse-z plane: x interpolants of the coarse rows
     TS v12[RPW];
@@ -313,7 +332,6 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     }
     if (MODE == 0) *reinterpret_cast<TS2*>(xch + warp * RC + cx0) = TS2{In[0][0], In[0][1]};
     __syncthreads();
-    if (STAGES == 1 && t < t_end) issue(t + 1);  // every thread has read the stage buffer
 
     // ---- coefficients of both planes -> shared memory and the nodal output
     TS* cc = cbuf;
@@ -374,14 +392,23 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         }
       }
       if (hf) {
+        TS vf[4];
+        {
+          const TI2 f0 = *reinterpret_cast<const TI2*>(sf + r0 * RC + cx0);
+          const TI2 f1 = *reinterpret_cast<const TI2*>(sf + (r0 + 1) * RC + cx0);
+          vf[0] = TS(f0.x);
+          vf[1] = TS(f0.y);
+          vf[2] = TS(f1.x);
+          vf[3] = TS(f1.y);
+        }
         TS d[4];
         if (MODE == 0) {
           const TS za = a.wa[0][Pf], zb = a.wb[0][Pf];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) d[e] = vf[k][e] - za * Ip[k][e] - zb * In[k][e];
+          for (int e = 0; e < 4; ++e) d[e] = vf[e] - za * Ip[k][e] - zb * In[k][e];
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) d[e] = vf[k][e];
+          for (int e = 0; e < 4; ++e) d[e] = vf[e];
         }
         *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
         *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
@@ -394,6 +421,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       }
     }
     __syncthreads();
+
+    if (STAGES == 1 && t < t_end) issue(t + 1);  // every thread is done with the stage buffer
 
     // ---- x stencil on every row of this warp (both planes)
     if (kxo) {
@@ -410,23 +439,23 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
             const TS2 a01 = *reinterpret_cast<const TS2*>(row);
             const TS2 a23 = *reinterpret_cast<const TS2*>(row + 2);
             if (zero_row) {
-              g = kx[1] * a01.y + kx[3] * a23.y;
+              g = kx(1) * a01.y + kx(3) * a23.y;
             } else {
-              g = kx[0] * a01.x + kx[1] * a01.y + kx[2] * a23.x + kx[3] * a23.y + kx[4] * row[4];
+              g = kx(0) * a01.x + kx(1) * a01.y + kx(2) * a23.x + kx(3) * a23.y + kx(4) * row[4];
             }
             if (hf) {
               const TS* rf = cf + r * CP + dx - 2;
               const TS2 b01 = *reinterpret_cast<const TS2*>(rf);
               const TS2 b23 = *reinterpret_cast<const TS2*>(rf + 2);
-              gf = kx[0] * b01.x + kx[1] * b01.y + kx[2] * b23.x + kx[3] * b23.y + kx[4] * rf[4];
+              gf = kx(0) * b01.x + kx(1) * b01.y + kx(2) * b23.x + kx(3) * b23.y + kx(4) * rf[4];
             }
           } else {
             g = TS(0);
 #pragma unroll
             for (int o = 0; o < 5; ++o)
               if (kxm & (1u << o)) {
-                g += kx[o] * cc[r * CP + dx - 2 + o];
-                if (hf) gf += kx[o] * cf[r * CP + dx - 2 + o];
+                g += kx(o) * cc[r * CP + dx - 2 + o];
+                if (hf) gf += kx(o) * cf[r * CP + dx - 2 + o];
               }
           }
           gxb[r * 32 + lane] = g;
@@ -458,19 +487,19 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         TS gc = TS(0), gf = TS(0);
         const TS* gcol = gxb + (dyo[k] - 2) * 32 + lane;
         if (kym[k] == 31u) {  // interior row: all five taps inside the grid
-          gc = ky[k][0] * gcol[0] + ky[k][1] * gcol[32] + ky[k][2] * gcol[64] + ky[k][3] * gcol[96] +
-               ky[k][4] * gcol[128];
+          gc = ky(k, 0) * gcol[0] + ky(k, 1) * gcol[32] + ky(k, 2) * gcol[64] + ky(k, 3) * gcol[96] +
+               ky(k, 4) * gcol[128];
           if (hf) {
             const TS* fcol = gcol + RR * 32;
-            gf = ky[k][0] * fcol[0] + ky[k][1] * fcol[32] + ky[k][2] * fcol[64] + ky[k][3] * fcol[96] +
-                 ky[k][4] * fcol[128];
+            gf = ky(k, 0) * fcol[0] + ky(k, 1) * fcol[32] + ky(k, 2) * fcol[64] + ky(k, 3) * fcol[96] +
+                 ky(k, 4) * fcol[128];
           }
         } else {
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
             if (kym[k] & (1u << o)) {
-              gc += ky[k][o] * gxb[(dyo[k] + o - 2) * 32 + lane];
-              if (hf) gf += ky[k][o] * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
+              gc += ky(k, o) * gxb[(dyo[k] + o - 2) * 32 + lane];
+              if (hf) gf += ky(k, o) * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
             }
           }
         }
