@@ -40,6 +40,12 @@ def _load():
         lib.oracle_transfer_1d.restype = ctypes.c_int64
         lib.oracle_interp_1d.argtypes = [ctypes.c_int64, dp, dp]
         lib.oracle_interp_1d.restype = ctypes.c_int64
+        lib.oracle_class_offsets.argtypes = [ctypes.c_int, i64p, ctypes.c_int, i64p]
+        lib.oracle_class_offsets.restype = ctypes.c_int
+        lib.oracle_pack_classes.argtypes = [ctypes.c_int, i64p, ctypes.c_int, dp, dp]
+        lib.oracle_pack_classes.restype = ctypes.c_int
+        lib.oracle_unpack_classes.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_unpack_classes.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -142,8 +148,55 @@ def interp_1d(x):
     return P
 
 
+def class_offsets(shape, levels=-1):
+    """Start of every coefficient class in the class-packed layout (length L+2, last = N).
+
+    Class 0 is the coarsest grid N_0, class l the coefficients on N_l \\ N_{l-1}
+    (Sec. I, coefficient classes)."""
+    lib = _load()
+    out = (ctypes.c_int64 * 66)()
+    r = lib.oracle_class_offsets(len(shape), _shape_arr(shape), int(levels), out)
+    if r < 0:
+        raise ValueError(f"invalid shape {shape} / levels {levels}")
+    return np.array(out[: r + 1], dtype=np.int64)
+
+
+def pack_classes(nodal, levels=-1):
+    """Nodal layout -> class-packed layout (flat array; classes coarsest first)."""
+    lib = _load()
+    u = np.ascontiguousarray(nodal, dtype=np.float64)
+    out = np.empty(u.size)
+    rc = lib.oracle_pack_classes(u.ndim, _shape_arr(u.shape), int(levels), _dptr(u), _dptr(out))
+    if rc != 0:
+        raise ValueError(f"pack_classes: invalid arguments ({rc})")
+    return out
+
+
+def unpack_classes(packed, shape, nclasses=None, levels=-1):
+    """Class-packed layout -> nodal layout keeping classes 0..nclasses-1 (dropped classes are 0)."""
+    lib = _load()
+    offs = class_offsets(shape, levels)
+    if nclasses is None:
+        nclasses = len(offs) - 1
+    p = np.ascontiguousarray(packed, dtype=np.float64).ravel()
+    if p.size < offs[nclasses]:
+        raise ValueError("packed input shorter than the requested classes")
+    out = np.empty(tuple(shape))
+    rc = lib.oracle_unpack_classes(len(shape), _shape_arr(shape), int(levels), int(nclasses), _dptr(p), _dptr(out))
+    if rc != 0:
+        raise ValueError(f"unpack_classes: invalid arguments ({rc})")
+    return out
+
+
+def recompose_classes(packed, shape, nclasses=None, coords=None, levels=-1):
+    """Progressive recomposition: the field rebuilt from classes 0..nclasses-1 of a
+    class-packed decomposition, the dropped classes taken as zero."""
+    return recompose(unpack_classes(packed, shape, nclasses, levels), coords, levels)
+
+
 def library_path():
     return _build.build()
 
 
-__all__ = ["max_levels", "default_levels", "decompose", "recompose", "mass_1d", "transfer_1d", "interp_1d"]
+__all__ = ["max_levels", "default_levels", "decompose", "recompose", "mass_1d", "transfer_1d", "interp_1d",
+           "class_offsets", "pack_classes", "unpack_classes", "recompose_classes"]

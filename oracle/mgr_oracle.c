@@ -52,6 +52,11 @@
  *   K (m x n)  K = P^T M, formed numerically (Sec. III.A.2 "mass-trans").
  *   M^c        the mass matrix built the same way on the coarse coordinates.
  *
+ *   Coefficient classes (Sec. I): class 0 = nodal values on N_0, class l =
+ *   coefficients on N_l \ N_{l-1}; the class-packed layout concatenates them,
+ *   coarsest first, each in row-major order of its level grid.  Recomposing
+ *   from a prefix of the classes treats the dropped classes as zero.
+ *
  * Pins (checked by the -m "not gpu" tests): the worked 1D example of
  * Fig. example-1d; dense L2 projection Q_l u = (Phi^T G Phi)^-1 ... solved
  * densely with exact quadrature on tiny 1D/2D/3D grids; closed-form mass
@@ -618,4 +623,102 @@ int oracle_recompose(int ndim, const int64_t* shape, const double* const* coords
   free(v);
   hierarchy_free(&h);
   return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Coefficient classes (Sec. I: the data are modelled by hierarchically */
+/* organised coefficient classes; reconstructing from a prefix of them   */
+/* gives an approximation of chosen fidelity)                            */
+/* ------------------------------------------------------------------ */
+/*
+ * Class 0 holds the nodal values on the coarsest grid N_0; class l (1..L)
+ * holds the coefficients on N_l \ N_{l-1}.  The class-packed layout stores
+ * the classes one after another, coarsest first, each in row-major order of
+ * its level grid (nodes of N_{l-1} skipped).  With the nodal layout every
+ * entry already sits at its own full-grid position, so packing is a pure
+ * reordering: it is written here directly from that definition, visiting the
+ * level grids node by node.
+ */
+
+/* Is the level-l node idx in N_{l-1} (coarse along every dimension)? */
+static int in_coarser(const hierarchy* h, int l, const int64_t* idx) {
+  for (int k = 0; k < h->ndim; ++k)
+    if (!is_coarse(idx[k], h->len[l][k])) return 0;
+  return 1;
+}
+
+/* offsets[c] = first packed position of class c, c = 0..L; offsets[L+1] = N.
+   Returns the number of classes L+1, or a negative error. */
+int oracle_class_offsets(int ndim, const int64_t* shape, int levels, int64_t* offsets) {
+  hierarchy h;
+  int rc = hierarchy_build(&h, ndim, shape, NULL, levels);
+  if (rc != 0) return rc;
+  int64_t pos = 0;
+  for (int l = 0; l <= h.L; ++l) {
+    offsets[l] = pos;
+    int64_t n = 1, mm = 1;
+    for (int k = 0; k < ndim; ++k) n *= h.len[l][k];
+    if (l > 0)
+      for (int k = 0; k < ndim; ++k) mm *= h.len[l - 1][k];
+    pos += (l == 0) ? n : n - mm;
+  }
+  offsets[h.L + 1] = pos;
+  int ncls = h.L + 1;
+  hierarchy_free(&h);
+  return ncls;
+}
+
+/* Visit every entry of the packed layout in order, calling
+   fn(packed position, nodal offset, class). */
+static int for_each_class_entry(int ndim, const int64_t* shape, int levels,
+                                void (*fn)(void*, int64_t, int64_t, int), void* arg) {
+  hierarchy h;
+  int rc = hierarchy_build(&h, ndim, shape, NULL, levels);
+  if (rc != 0) return rc;
+  int64_t pos = 0, idx[ORACLE_MAXDIM];
+  for (int l = 0; l <= h.L; ++l) {
+    int64_t n[ORACLE_MAXDIM];
+    for (int k = 0; k < ndim; ++k) n[k] = h.len[l][k];
+    for (int64_t f = 0; f < prod(ndim, n); ++f) {
+      unravel(ndim, n, f, idx);
+      if (l > 0 && in_coarser(&h, l, idx)) continue;
+      fn(arg, pos++, full_offset(&h, l, idx), l);
+    }
+  }
+  hierarchy_free(&h);
+  return 0;
+}
+
+typedef struct {
+  const double* src;
+  double* dst;
+  int nclasses;
+} copy_args;
+
+static void pack_one(void* a, int64_t pos, int64_t off, int cls) {
+  copy_args* c = (copy_args*)a;
+  (void)cls;
+  c->dst[pos] = c->src[off];
+}
+
+static void unpack_one(void* a, int64_t pos, int64_t off, int cls) {
+  copy_args* c = (copy_args*)a;
+  c->dst[off] = (cls < c->nclasses) ? c->src[pos] : 0.0;
+}
+
+/* nodal layout -> class-packed layout (a permutation of the N entries). */
+int oracle_pack_classes(int ndim, const int64_t* shape, int levels, const double* nodal, double* packed) {
+  copy_args a = {nodal, packed, 0};
+  return for_each_class_entry(ndim, shape, levels, pack_one, &a);
+}
+
+/* class-packed layout -> nodal layout, keeping classes 0..nclasses-1; the
+   positions of the dropped classes are set to 0 (a dropped class is a zero
+   coefficient class).  `packed` needs only its first offsets[nclasses]
+   entries. */
+int oracle_unpack_classes(int ndim, const int64_t* shape, int levels, int nclasses, const double* packed,
+                          double* nodal) {
+  if (nclasses < 1) return -1;
+  copy_args a = {packed, nodal, nclasses};
+  return for_each_class_entry(ndim, shape, levels, unpack_one, &a);
 }
