@@ -140,6 +140,48 @@ int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out
 int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
                        void* workspace, mgr_stream_t stream);
 
+/* ------------------------------------------------ coefficient classes */
+
+/* Class-packed layout (Sec. I: the refactored data are a series of
+   hierarchically organised coefficient classes, and an approximation of a
+   chosen fidelity is rebuilt from the first few of them).  Class 0 holds the
+   coarsest nodal values Q_0 u on N_0; class l (1..L) holds the level-l
+   coefficients on N_l \ N_{l-1}.  The classes are stored one after another,
+   coarsest first, each in row-major order of its level grid with the nodes
+   of N_{l-1} left out, so the first k classes are a prefix of the buffer.
+   Total size: prod(shape) elements, like the nodal layout. */
+
+/* offsets[c] = first element of class c for c = 0..L, offsets[L+1] =
+   prod(shape); writes min(cap, L+2) entries and sets *nclasses = L+1.
+   Host-only (no device work). */
+int mgr_class_offsets(const mgr_plan* plan, int64_t* offsets, int cap, int* nclasses);
+
+/* Decompose into the class-packed layout: the same operation as
+   mgr_decompose, with the level pass writing each coefficient straight to its
+   class position (no extra pass).  out: DEVICE, prod(shape) elements; it must
+   not overlap `in` (MGR_EINVAL).  Workspace as for mgr_decompose. */
+int mgr_decompose_packed(const mgr_plan* plan, const void* in, void* out, void* workspace, mgr_stream_t stream);
+
+/* Progressive recomposition: rebuild the field from classes 0..nclasses-1 of
+   a class-packed decomposition, the dropped classes taken as zero.  The
+   result is Q_{nclasses-1} u, interpolated to the full grid; nclasses = L+1
+   is the exact inverse of mgr_decompose_packed.  Levels whose class is
+   dropped have a zero correction and run as interpolation only.
+     in        DEVICE; only its first offsets[nclasses] elements are read
+     nclasses  1..L+1 (else MGR_EINVAL)
+     out       DEVICE, prod(shape) elements, not overlapping in[0..N)
+   Workspace and stream as for mgr_recompose. */
+int mgr_recompose_packed(const mgr_plan* plan, const void* in, int nclasses, void* out, void* workspace,
+                         mgr_stream_t stream);
+
+/* Layout conversions, one launch each, no workspace.  pack: nodal -> class-
+   packed (a permutation).  unpack: classes 0..nclasses-1 of a class-packed
+   buffer -> nodal layout, with the nodes of dropped classes set to 0
+   (nclasses 1..L+1; only the first offsets[nclasses] elements are read).
+   The two buffers must not overlap. */
+int mgr_pack_classes(const mgr_plan* plan, const void* nodal, void* packed, mgr_stream_t stream);
+int mgr_unpack_classes(const mgr_plan* plan, const void* packed, int nclasses, void* nodal, mgr_stream_t stream);
+
 /* ------------------------------------------------------------ no-alloc form */
 
 /* Size of the fixed device scratch area used by mgr_decompose_noalloc. */
@@ -270,15 +312,19 @@ int mgr_serve_stop(mgr_server* server);
    launching stream immediately before and after it. */
 typedef struct {
   char name[32]; /* kernel role: level_load_dec, level_load_rec, solve_x/y/z, interp,
-                    coarsest, coef_inplace                                          */
+                    interp_zero (a dropped class), coarsest, coef_inplace          */
   int level;     /* level l of the launch (0 for the coarsest-grid copy)            */
   float ms;      /* event-to-event duration                                         */
   double bytes;  /* compulsory bytes of the launch's inputs and outputs             */
   double flops;  /* floating-point operations of its minimal arithmetic (FMA = 2)   */
 } mgr_kernel_time;
 
-/* Run one decomposition (op = 0) or recomposition (op = 1) exactly as
-   mgr_decompose / mgr_recompose would, but launched directly (no graph) with
+#define MGR_OP_DECOMPOSE_PACKED 2 /* mgr_profile only: mgr_decompose_packed                */
+#define MGR_OP_RECOMPOSE_PACKED 3 /* mgr_profile only: mgr_recompose_packed, every class   */
+
+/* Run one decomposition (op = 0) or recomposition (op = 1), or their
+   class-packed forms (op = 2, 3), exactly as mgr_decompose / mgr_recompose /
+   mgr_decompose_packed / mgr_recompose_packed would, but launched directly (no graph) with
    a pair of CUDA events around every kernel, and wait for it.  Writes up to
    `cap` records to `times` and the number of launches to *n (which may exceed
    cap).  Not part of the hot path: it synchronises `stream`. */

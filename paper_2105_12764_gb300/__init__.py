@@ -15,7 +15,8 @@ import os
 __all__ = [
     "MGR_OK", "MGR_EINVAL", "MGR_ENOMEM", "MGR_EBUDGET", "MGR_ECUDA", "MGR_EPENDING", "MGR_ETIMEDOUT",
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
-    "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE", "Server", "lib", "library_path", "Context", "Plan", "EXPORTED",
+    "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE",
+    "MGR_OP_DECOMPOSE_PACKED", "MGR_OP_RECOMPOSE_PACKED", "Server", "lib", "library_path", "Context", "Plan", "EXPORTED",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +68,7 @@ class mgr_request(ctypes.Structure):
 
 
 MGR_OP_DECOMPOSE, MGR_OP_RECOMPOSE = 0, 1
+MGR_OP_DECOMPOSE_PACKED, MGR_OP_RECOMPOSE_PACKED = 2, 3  # mgr_profile only
 
 
 class mgr_serve_request(ctypes.Structure):
@@ -110,6 +112,11 @@ EXPORTED = {
     "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
     "mgr_decompose_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mgr_class_offsets": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, ctypes.POINTER(_i)]),
+    "mgr_decompose_packed": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mgr_recompose_packed": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "mgr_pack_classes": (_i, [_vp, _vp, _vp, _vp]),
+    "mgr_unpack_classes": (_i, [_vp, _vp, _i, _vp, _vp]),
     "mgr_batch_submit": (_i, [_vp, ctypes.POINTER(mgr_request), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mgr_batch_poll": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_i)]),
     "mgr_batch_tuning": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -273,6 +280,29 @@ class Plan:
         """mgr_decompose_noalloc: no workspace argument, no device allocation (fields whose workspace
         fits MGR_NOALLOC_SCRATCH_BYTES; calls that overlap on the GPU must be serialised)."""
         _check("mgr_decompose_noalloc", lib.mgr_decompose_noalloc(self.handle, _ptr(inp), _ptr(out), _stream(stream)))
+
+    def class_offsets(self):
+        """mgr_class_offsets: start of every coefficient class in the class-packed layout (L+2 entries)."""
+        arr = (ctypes.c_int64 * (self.levels + 2))()
+        n = _i()
+        _check("mgr_class_offsets", lib.mgr_class_offsets(self.handle, arr, self.levels + 2, ctypes.byref(n)))
+        return list(arr)
+
+    def decompose_packed(self, inp, out, workspace, stream=None):
+        _check("mgr_decompose_packed", lib.mgr_decompose_packed(self.handle, _ptr(inp), _ptr(out), _ptr(workspace),
+                                                                _stream(stream)))
+
+    def recompose_packed(self, inp, nclasses, out, workspace, stream=None):
+        """mgr_recompose_packed: the field from classes 0..nclasses-1 (dropped classes are zero)."""
+        _check("mgr_recompose_packed", lib.mgr_recompose_packed(self.handle, _ptr(inp), int(nclasses), _ptr(out),
+                                                                _ptr(workspace), _stream(stream)))
+
+    def pack_classes(self, nodal, packed, stream=None):
+        _check("mgr_pack_classes", lib.mgr_pack_classes(self.handle, _ptr(nodal), _ptr(packed), _stream(stream)))
+
+    def unpack_classes(self, packed, nclasses, nodal, stream=None):
+        _check("mgr_unpack_classes", lib.mgr_unpack_classes(self.handle, _ptr(packed), int(nclasses), _ptr(nodal),
+                                                            _stream(stream)))
 
     def decompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
         _check("mgr_decompose_host", lib.mgr_decompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),

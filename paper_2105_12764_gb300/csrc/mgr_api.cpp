@@ -29,11 +29,15 @@ int check_sticky() {
   return MGR_OK;
 }
 
-int check_op_args(const mgr_plan* p, const void* in, const void* out, const void* ws) {
+// Operation codes of run_op / the graph cache; OP_REC_PACKED carries the
+// number of classes in bits 8 and up.
+enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3 };
+
+int check_op_args(const mgr_plan* p, const void* in, const void* out, const void* ws, bool alias_ok = true) {
   if (!p || !in || !out) return MGR_EINVAL;
   const size_t bytes = size_t(p->count) * p->elem;
   if ((reinterpret_cast<uintptr_t>(in) % p->elem) || (reinterpret_cast<uintptr_t>(out) % p->elem)) return MGR_EINVAL;
-  if (in != out && ranges_overlap(in, bytes, out, bytes)) return MGR_EINVAL;
+  if ((in != out || !alias_ok) && ranges_overlap(in, bytes, out, bytes)) return MGR_EINVAL;
   if (p->ws_bytes > 0) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign)) return MGR_EINVAL;
     if (ranges_overlap(ws, p->ws_bytes, in, bytes) || ranges_overlap(ws, p->ws_bytes, out, bytes)) return MGR_EINVAL;
@@ -41,18 +45,23 @@ int check_op_args(const mgr_plan* p, const void* in, const void* out, const void
   return MGR_OK;
 }
 
-enum { OP_DEC = 0, OP_REC = 1 };
-
 cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st) {
-  return op == OP_DEC ? mgr::enqueue_decompose(p, in, out, ws, st) : mgr::enqueue_recompose(p, in, out, ws, st);
+  switch (op & 0xff) {
+    case OP_DEC: return mgr::enqueue_decompose(p, in, out, ws, st);
+    case OP_REC: return mgr::enqueue_recompose(p, in, out, ws, st);
+    case OP_DEC_PACKED: return mgr::enqueue_decompose_packed(p, in, out, ws, st);
+    default: return mgr::enqueue_recompose_packed(p, in, op >> 8, out, ws, st);
+  }
 }
+
+bool packed_op(int op) { return (op & 0xff) == OP_DEC_PACKED || (op & 0xff) == OP_REC_PACKED; }
 
 // Launch through a cached CUDA graph of the plan's launch sequence.  When the
 // caller's stream is itself being captured the kernels are enqueued directly
 // (they become part of the caller's graph).
 int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cudaStream_t st) {
   mgr_plan* p = const_cast<mgr_plan*>(cp);
-  int rc = check_op_args(p, in, out, ws);
+  int rc = check_op_args(p, in, out, ws, !packed_op(op));
   if (rc != MGR_OK) return rc;
   if ((rc = check_sticky()) != MGR_OK) return rc;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -286,6 +295,16 @@ int mgr_recompose(const mgr_plan* p, const void* in, void* out, void* ws, mgr_st
   return run_op(p, OP_REC, in, out, ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int mgr_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, mgr_stream_t stream) {
+  return run_op(p, OP_DEC_PACKED, in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgr_recompose_packed(const mgr_plan* p, const void* in, int nclasses, void* out, void* ws,
+                         mgr_stream_t stream) {
+  if (!p || nclasses < 1 || nclasses > p->levels + 1) return MGR_EINVAL;
+  return run_op(p, OP_REC_PACKED | (nclasses << 8), in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int mgr_decompose_host(const mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
                        mgr_stream_t stream) {
   return run_host(p, OP_DEC, host_in, host_out, dev_in, dev_out, ws, reinterpret_cast<cudaStream_t>(stream));
@@ -298,8 +317,9 @@ int mgr_recompose_host(const mgr_plan* p, const void* host_in, void* host_out, v
 
 int mgr_profile(const mgr_plan* p, int op, const void* in, void* out, void* ws, mgr_stream_t stream,
                 mgr_kernel_time* times, int cap, int* n) {
-  if (!n || (cap > 0 && !times) || (op != OP_DEC && op != OP_REC)) return MGR_EINVAL;
-  int rc = check_op_args(p, in, out, ws);
+  if (!n || (cap > 0 && !times) || op < OP_DEC || op > OP_REC_PACKED || !p) return MGR_EINVAL;
+  if (op == OP_REC_PACKED) op |= (p->levels + 1) << 8;
+  int rc = check_op_args(p, in, out, ws, !packed_op(op));
   if (rc != MGR_OK) return rc;
   if ((rc = check_sticky()) != MGR_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

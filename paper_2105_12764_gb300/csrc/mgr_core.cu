@@ -179,17 +179,19 @@ dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
   return dim3(gx, gy, gz);
 }
 
-template <int MODE, typename TI, typename TD, typename TS, typename TW>
+template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK>
 void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
   using C = LevelCfg<TS>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
-  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>;
+  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   dim3 grid = level_grid(p, a);
   kern<<<grid, C::NW * 32, sm, st>>>(a);
 }
 
-template <typename TD, typename TO, typename TS, typename TW>
+// c: nodal coefficients (PK false), the packed class of level l (PK true), or
+// null for a dropped class (all coefficients zero)
+template <typename TD, typename TO, typename TS, typename TW, bool PK>
 void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st) {
   const LevelGeom& g = p->geom[l];
   const TS* T = table<TS>(p);
@@ -203,8 +205,8 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
     a.wb[k] = T + g.ax[k].o_wb;
   }
   a.c = c;
-  a.y_sz = p->full[1] * p->full[2];
-  a.y_sy = p->full[2];
+  a.y_sz = PK ? int64_t(g.ax[1].n) * g.ax[2].n : p->full[1] * p->full[2];
+  a.y_sy = PK ? int64_t(g.ax[2].n) : p->full[2];
   a.w = w;
   a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
   a.c_sy = g.ax[2].m;
@@ -218,7 +220,7 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
-  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW>;
+  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
 }
@@ -292,7 +294,26 @@ cudaError_t solve_level(const mgr_plan* p, int l, TW* f, TW* w, int final_op, cu
   return cudaSuccess;
 }
 
-template <typename TD, typename TS, typename TW>
+// Coarsest grid <-> its place in the output: the nodal positions at stride
+// 2^L (nodal layout) or class 0, the compact coarsest grid (packed layout).
+template <typename TD, typename TW>
+cudaError_t coarsest_copy_launch(const mgr_plan* p, TD* y, TW* w, bool packed, int dir, cudaStream_t st) {
+  const int L = p->levels;
+  const int3 n0 = make_int3(int(p->coarsest[0]), int(p->coarsest[1]), int(p->coarsest[2]));
+  const int64_t s0 = packed ? 1 : (int64_t(1) << L);
+  const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
+  const longlong3 N = packed ? make_longlong3(n0.x, n0.y, n0.z) : make_longlong3(p->full[0], p->full[1], p->full[2]);
+  const int64_t total = int64_t(n0.x) * n0.y * n0.z;
+  rec_begin(st);
+  k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(y, N.y * N.z, N.z, w, n0, s, N, dir);
+  cudaError_t e = cudaGetLastError();
+  rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
+  return e;
+}
+
+// PK: write the coefficients in the class-packed layout (class l at
+// p->class_off[l]; `out` must not overlap `in`).
+template <typename TD, typename TS, typename TW, bool PK>
 cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
   const int L = p->levels;
   const size_t bytes = size_t(p->count) * sizeof(TD);
@@ -300,14 +321,20 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if (in != out) return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
     return cudaSuccess;
   }
-  const bool inplace = (in == out);
+  const bool inplace = !PK && (in == out);
   Bufs b = split_ws(p, ws);
   TW* F = static_cast<TW*>(b.F);
   TW* cur = nullptr;  // compact level-l values for l < L
   for (int l = L; l >= 1; --l) {
     TW* nxt = static_cast<TW*>(((L - l) % 2 == 0) ? b.A : b.B);
     auto a = level_args<TS, TW>(p, l);
+    const LevelGeom& g = p->geom[l];
     a.y = out;
+    if (PK) {
+      a.y = static_cast<TD*>(out) + p->class_off[l];
+      a.y_sz = int64_t(g.ax[1].n) * g.ax[2].n;
+      a.y_sy = g.ax[2].n;
+    }
     a.w = nxt;
     a.f = F;
     a.write_y = (l == L && inplace) ? 0 : 1;
@@ -315,16 +342,15 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if (l == L) {
       a.in = in;
       a.in_full = 1;
-      a.in_sz = a.y_sz;
-      a.in_sy = a.y_sy;
-      launch_level<0, TD, TD, TS, TW>(p, a, st);
+      a.in_sz = p->full[1] * p->full[2];
+      a.in_sy = p->full[2];
+      launch_level<0, TD, TD, TS, TW, PK>(p, a, st);
     } else {
-      const LevelGeom& g = p->geom[l];
       a.in = cur;
       a.in_full = 0;
       a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
       a.in_sy = g.ax[2].n;
-      launch_level<0, TW, TD, TS, TW>(p, a, st);
+      launch_level<0, TW, TD, TS, TW, PK>(p, a, st);
     }
     cudaError_t e = cudaGetLastError();
     {
@@ -350,22 +376,16 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if ((e = solve_level<TW>(p, l, F, nxt, SOLVE_ADD, st)) != cudaSuccess) return e;
     cur = nxt;
   }
-  // coarsest values into their nodal positions
-  const int3 n0 = make_int3(int(p->coarsest[0]), int(p->coarsest[1]), int(p->coarsest[2]));
-  const int64_t s0 = int64_t(1) << L;
-  const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
-  const longlong3 N = make_longlong3(p->full[0], p->full[1], p->full[2]);
-  const int64_t total = int64_t(n0.x) * n0.y * n0.z;
-  rec_begin(st);
-  k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(static_cast<TD*>(out), p->full[1] * p->full[2],
-                                                               p->full[2], cur, n0, s, N, 1);
-  cudaError_t e = cudaGetLastError();
-  rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
-  return e;
+  // coarsest values into their nodal positions / class 0
+  return coarsest_copy_launch<TD, TW>(p, static_cast<TD*>(out), cur, PK, 1, st);
 }
 
-template <typename TD, typename TS, typename TW>
-cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+// Recompose from classes 0..ncls-1 (ncls = L+1: all of them).  Levels whose
+// class is dropped have zero coefficients, hence a zero correction: they are
+// interpolation only.  PK: `in` is class-packed (its first class_off[ncls]
+// elements are read) and must not overlap `out`.
+template <typename TD, typename TS, typename TW, bool PK>
+cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st, int ncls) {
   const int L = p->levels;
   const size_t bytes = size_t(p->count) * sizeof(TD);
   if (L == 0) {
@@ -374,33 +394,50 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   }
   Bufs b = split_ws(p, ws);
   TW* F = static_cast<TW*>(b.F);
-  // coarsest grid from the nodal positions
+  // coarsest grid from the nodal positions / class 0
   TW* cur = static_cast<TW*>((L % 2 == 1) ? b.A : b.B);  // level 0 lives where decompose left it
   {
-    const int3 n0 = make_int3(int(p->coarsest[0]), int(p->coarsest[1]), int(p->coarsest[2]));
-    const int64_t s0 = int64_t(1) << L;
-    const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
-    const longlong3 N = make_longlong3(p->full[0], p->full[1], p->full[2]);
-    const int64_t total = int64_t(n0.x) * n0.y * n0.z;
-    rec_begin(st);
-    k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(const_cast<TD*>(static_cast<const TD*>(in)),
-                                                                 p->full[1] * p->full[2], p->full[2], cur, n0, s, N, 0);
-    cudaError_t e = cudaGetLastError();
-    rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
+    cudaError_t e = coarsest_copy_launch<TD, TW>(p, const_cast<TD*>(static_cast<const TD*>(in)), cur, PK, 0, st);
     if (e != cudaSuccess) return e;
   }
   for (int l = 1; l <= L; ++l) {
+    const LevelGeom& g = p->geom[l];
+    const void* cl = PK ? static_cast<const void*>(static_cast<const TD*>(in) + p->class_off[l]) : in;
+    if (l >= ncls) {
+      // dropped class: v = interpolant of the coarse values
+      rec_begin(st);
+      if (l == L) {
+        launch_interp<TD, TD, TS, TW, PK>(p, l, nullptr, cur, out, 1, st);
+      } else {
+        TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
+        launch_interp<TD, TW, TS, TW, PK>(p, l, nullptr, cur, nxt, 0, st);
+        cur = nxt;
+      }
+      cudaError_t e = cudaGetLastError();
+      {
+        const Work wk = work_interp(p, l);
+        rec_end(st, "interp_zero", l, wk.bytes - double(g.fine_count()) * sizeof(TD), wk.flops);
+      }
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     auto a = level_args<TS, TW>(p, l);
-    a.in = in;
-    a.in_full = 1;
-    a.in_sz = a.y_sz;
-    a.in_sy = a.y_sy;
+    a.in = cl;
+    if (PK) {
+      a.in_full = 0;
+      a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
+      a.in_sy = g.ax[2].n;
+    } else {
+      a.in_full = 1;
+      a.in_sz = a.y_sz;
+      a.in_sy = a.y_sy;
+    }
     a.f = F;
     a.w = nullptr;
     a.y = nullptr;
     a.write_y = 0;
     rec_begin(st);
-    launch_level<1, TD, TD, TS, TW>(p, a, st);
+    launch_level<1, TD, TD, TS, TW, PK>(p, a, st);
     cudaError_t e = cudaGetLastError();
     {
       const Work wk = work_level_load(p, l, false);
@@ -410,10 +447,10 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if ((e = solve_level<TW>(p, l, F, cur, SOLVE_SUB, st)) != cudaSuccess) return e;
     rec_begin(st);
     if (l == L) {
-      launch_interp<TD, TD, TS, TW>(p, l, in, cur, out, 1, st);
+      launch_interp<TD, TD, TS, TW, PK>(p, l, cl, cur, out, 1, st);
     } else {
       TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
-      launch_interp<TD, TW, TS, TW>(p, l, in, cur, nxt, 0, st);
+      launch_interp<TD, TW, TS, TW, PK>(p, l, cl, cur, nxt, 0, st);
       cur = nxt;
     }
     e = cudaGetLastError();
@@ -430,17 +467,35 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
 
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
   switch (p->form) {
-    case kFormF64: return decompose_t<double, double, double>(p, in, out, ws, st);
-    case kFormF32: return decompose_t<float, float, float>(p, in, out, ws, st);
-    default: return decompose_t<float, float, double>(p, in, out, ws, st);
+    case kFormF64: return decompose_t<double, double, double, false>(p, in, out, ws, st);
+    case kFormF32: return decompose_t<float, float, float, false>(p, in, out, ws, st);
+    default: return decompose_t<float, float, double, false>(p, in, out, ws, st);
   }
 }
 
 cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+  const int all = p->levels + 1;
   switch (p->form) {
-    case kFormF64: return recompose_t<double, double, double>(p, in, out, ws, st);
-    case kFormF32: return recompose_t<float, float, float>(p, in, out, ws, st);
-    default: return recompose_t<float, float, double>(p, in, out, ws, st);
+    case kFormF64: return recompose_t<double, double, double, false>(p, in, out, ws, st, all);
+    case kFormF32: return recompose_t<float, float, float, false>(p, in, out, ws, st, all);
+    default: return recompose_t<float, float, double, false>(p, in, out, ws, st, all);
+  }
+}
+
+cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+  switch (p->form) {
+    case kFormF64: return decompose_t<double, double, double, true>(p, in, out, ws, st);
+    case kFormF32: return decompose_t<float, float, float, true>(p, in, out, ws, st);
+    default: return decompose_t<float, float, double, true>(p, in, out, ws, st);
+  }
+}
+
+cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,
+                                     cudaStream_t st) {
+  switch (p->form) {
+    case kFormF64: return recompose_t<double, double, double, true>(p, in, out, ws, st, ncls);
+    case kFormF32: return recompose_t<float, float, float, true>(p, in, out, ws, st, ncls);
+    default: return recompose_t<float, float, double, true>(p, in, out, ws, st, ncls);
   }
 }
 

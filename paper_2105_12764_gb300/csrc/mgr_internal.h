@@ -78,6 +78,9 @@ struct mgr_plan {
   size_t welem = 0;                   // bytes per workspace element
   std::vector<mgr::LevelGeom> geom;   // geom[l] for l = 1..L (geom[0] unused)
   int64_t coarsest[mgr::kAxes] = {1, 1, 1};
+  // class-packed layout: class c (0 = coarsest grid, l = coefficients of level
+  // l) starts at class_off[c]; class_off[L+1] = count
+  std::vector<int64_t> class_off;
   mgr::Tables tables;
   // workspace layout (bytes)
   size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_bytes = 0;
@@ -129,5 +132,12 @@ void batch_destroy(mgr_ctx* ctx);
 // mgr_core.cu: enqueue one whole operation (all levels) on `st` (no graph).
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+// class-packed output / input (recompose from classes 0..ncls-1)
+cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,
+                                     cudaStream_t st);
+// mgr_classes.cu: layout conversion nodal <-> class-packed
+cudaError_t enqueue_pack_classes(const mgr_plan* p, const void* nodal, void* packed, cudaStream_t st);
+cudaError_t enqueue_unpack_classes(const mgr_plan* p, const void* packed, int ncls, void* nodal, cudaStream_t st);
 
 }  // namespace mgr

@@ -27,6 +27,15 @@
 // coarse in y and z, where c vanishes on coarse nodes), the y stencil on
 // the x results, and the z stencil accumulates in registers over the
 // streamed planes.  Four barriers per plane pair.
+//
+// Coefficient addressing.  Nodal (PK = false): a coefficient sits at its node's
+// full-grid position.  Class-packed (PK = true, Sec. I coefficient classes): the
+// coefficients of level l form one contiguous class, in row-major order of the
+// level grid with the nodes of the coarser grid left out.  With cb(i) = (i+1)/2
+// coarse nodes before index i, node (i, j, k) of class l is at
+//   i*n1*n2 - cb(i)*m1*m2 + (i fine ? j*n2 + k
+//                                   : j*n2 - cb(j)*m2 + (j fine ? k : k - cb(k)))
+// from the class start, so plane and row offsets stay separable.
 #pragma once
 
 template <int NW, int RPW>
@@ -128,7 +137,9 @@ __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bo
 
 // One CTA's work: coarse tile (bx, by) and z chunk bz of level args `a`,
 // with `smem_raw` the CTA's dynamic shared memory (level_smem_bytes).
-template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+// PK: coefficients in the class-packed layout (MODE 0 writes `y`, MODE 1 reads
+// `in` as the class of this level; y_sz / in_sz = n1*n2, y_sy / in_sy = n2).
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK = false>
 __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, int by, int bz,
                                            unsigned char* smem_raw) {
   using G = LevelTile<NW, RPW>;
@@ -171,8 +182,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const int ic0 = a.in_full ? int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])) : gx0;
   const int ic1 = a.in_full ? int(fmap(min(gx1, nx - 1), a.s[2], a.N[2])) : gx1;
   const bool icontig = ic1 == ic0 + 1;
-  const int yc0 = int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])), yc1 = int(fmap(min(gx1, nx - 1), a.s[2], a.N[2]));
+  const int yc0 = PK ? gx0 : int(fmap(min(gx0, nx - 1), a.s[2], a.N[2]));
+  const int yc1 = PK ? gx1 : int(fmap(min(gx1, nx - 1), a.s[2], a.N[2]));
   const bool ycontig = yc1 == yc0 + 1;
+  const int pcx1 = gx1 - cidx(gx1);  // packed column of gx1 in a row coarse in y and z
 
   // ---- x stencil of this lane's output column
   const int nbx = qx1 - qx0;
@@ -224,8 +237,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     const int c0 = min(gy0[k], ny - 1), c1 = min(g1, ny - 1);
     ir0[k] = int(a.in_full ? fmap(c0, a.s[1], a.N[1]) * a.in_sy : int64_t(c0) * a.in_sy);
     ir1[k] = int(a.in_full ? fmap(c1, a.s[1], a.N[1]) * a.in_sy : int64_t(c1) * a.in_sy);
-    yr0[k] = int(fmap(c0, a.s[1], a.N[1]) * a.y_sy);
-    yr1[k] = int(fmap(c1, a.s[1], a.N[1]) * a.y_sy);
+    yr0[k] = PK ? c0 * nx : int(fmap(c0, a.s[1], a.N[1]) * a.y_sy);
+    yr1[k] = PK ? c1 * nx : int(fmap(c1, a.s[1], a.N[1]) * a.y_sy);
     const int qy = min(qy0 + warp * RPW + k, my - 1);
     const int py = pidx(qy, ny);
     dyo[k] = py - ry0;
@@ -249,13 +262,29 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   __syncthreads();  // stencil weights staged
 
   auto iplane = [&](int g) -> int64_t {
+    if (PK && MODE == 1) return int64_t(g) * a.in_sz - int64_t(cidx(g)) * a.c_sz;
     return a.in_full ? fmap(g, a.s[0], a.N[0]) * a.in_sz : int64_t(g) * a.in_sz;
   };
-  auto load_plane = [&](TI* sb, int gz) {
+  // zc: gz is a coarse plane (a packed class then holds only its fine nodes)
+  auto load_plane = [&](TI* sb, int gz, bool zc) {
     const TI* base = in + iplane(gz);
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       TI* d0 = sb + 2 * (warp * RPW + k) * RC + cx0;
+      if (PK && MODE == 1 && zc) {
+        // rows of a coarse plane: the coarse row gy0 holds its fine columns only
+        const int r0 = ir0[k] - cidx(gy0[k]) * mx, r1 = ir1[k] - cidx(gy0[k] + 1) * mx;
+        if (vy0[k] && fx1) cp_async(d0 + 1, base + r0 + pcx1, int(sizeof(TI)));
+        if (vy1[k]) {
+          if (fy1[k]) {
+            if (vx0) cp_async(d0 + RC, base + r1 + ic0, int(sizeof(TI)));
+            if (vx1) cp_async(d0 + RC + 1, base + r1 + ic1, int(sizeof(TI)));
+          } else if (fx1) {
+            cp_async(d0 + RC + 1, base + r1 + pcx1, int(sizeof(TI)));
+          }
+        }
+        continue;
+      }
       if (vy0[k]) {
         if (vx0) cp_async(d0, base + ir0[k] + ic0, int(sizeof(TI)));
         if (vx1) cp_async(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)));
@@ -269,8 +298,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   auto has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
   auto issue = [&](int t) {
     TI* sb = stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0);
-    load_plane(sb, pidx(t, nz));
-    if (has_fine(t)) load_plane(sb + RR * RC, pidx(t, nz) - 1);
+    load_plane(sb, pidx(t, nz), true);
+    if (has_fine(t)) load_plane(sb + RR * RC, pidx(t, nz) - 1, false);
     cp_commit();
   };
 
@@ -336,8 +365,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     // ---- coefficients of both planes -> shared memory and the nodal output
     TS* cc = cbuf;
     TS* cf = cbuf + RR * CP;
-    TD* yzc = yout + fmap(Pc, a.s[0], a.N[0]) * a.y_sz;
-    TD* yzf = yout + fmap(max(Pf, 0), a.s[0], a.N[0]) * a.y_sz;
+    TD* yzc = yout + (PK ? int64_t(Pc) * a.y_sz - int64_t(cidx(Pc)) * a.c_sz : fmap(Pc, a.s[0], a.N[0]) * a.y_sz);
+    TD* yzf = yout + (PK ? int64_t(max(Pf, 0)) * a.y_sz - int64_t(cidx(max(Pf, 0))) * a.c_sz
+                         : fmap(max(Pf, 0), a.s[0], a.N[0]) * a.y_sz);
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int r0 = 2 * (warp * RPW + k);
@@ -373,7 +403,18 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       }
       *reinterpret_cast<TS2*>(cc + r0 * CP + cx0) = TS2{c[0], c[1]};
       *reinterpret_cast<TS2*>(cc + (r0 + 1) * CP + cx0) = TS2{c[2], c[3]};
-      if (wy && own_c) {
+      if (PK && wy && own_c) {
+        // packed class: the coarse row gy0 keeps only its fine column gx1
+        const int r0 = yr0[k] - cidx(gy0[k]) * mx, r1 = yr1[k] - cidx(gy0[k] + 1) * mx;
+        if (owy0[k] && owx1 && fx1) yzc[r0 + pcx1] = TD(c[1]);
+        if (owy1[k]) {
+          if (fy1[k]) {
+            store_pair<TD>(yzc + r1 + yc0, yzc + r1 + yc1, TD(c[2]), TD(c[3]), owx0, owx1, true);
+          } else if (owx1 && fx1) {
+            yzc[r1 + pcx1] = TD(c[3]);
+          }
+        }
+      } else if (wy && own_c) {
         // all-coarse nodes get their (uncorrected) value as a placeholder that a
         // coarser level overwrites; it keeps the row's sectors fully written
         store_pair<TD>(yzc + yr0[k] + yc0, yzc + yr0[k] + yc1, TD(vc[k][0]), TD(fx1 ? c[1] : vc[k][1]),
@@ -529,10 +570,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   }
 }
 
-template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK>
 __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,7 +588,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a)
 // ---------------------------------------------------------------------------
 template <typename TS, typename TW>
 struct InterpArgs {
-  const void* c;  // nodal coefficients (full grid)
+  const void* c;  // coefficients: nodal (full grid) or this level's packed class; null = all zero
   int64_t y_sz, y_sy;
   const TW* w;    // coarse values (compact m grid)
   int64_t c_sz, c_sy;
@@ -566,7 +607,8 @@ constexpr size_t interp_smem_bytes() {
   return sizeof(TD) * 2 * 2 * (2 * NW * RPW) * 64 + sizeof(TW) * 2 * (NW * RPW + 1) * 33;
 }
 
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+// PK: `c` is the class-packed class of this level (y_sz = n1*n2, y_sy = n2).
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK = false>
 __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx, int by, int bz,
                                             unsigned char* smem_raw) {
   constexpr int BY = NW * RPW, TR = BY + 1, TC = 33, RR = 2 * BY, RC = 64;
@@ -581,6 +623,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
   const int t_end = min(qz1, mz - 1);
   const int tcols = min(TC, mx - qx0), trows = min(TR, my - qy0);
   const TD* __restrict__ cin = static_cast<const TD*>(a.c);
+  const bool cz = cin == nullptr;  // coefficients of a dropped class: zero
   TO* __restrict__ out = static_cast<TO*>(a.out);
 
   // column block of this lane: fine nodes p(qx) and, when a fine node lies
@@ -591,14 +634,15 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
   const bool ox1 = ax && qx + 1 < mx && pidx(qx + 1, nx) - gx0 == 2;
   const TS wax1 = ox1 ? a.wa[2][gx0 + 1] : TS(0), wbx1 = ox1 ? a.wb[2][gx0 + 1] : TS(0);
   const int gx1 = min(gx0 + 1, nx - 1);
-  const int cc0 = int(fmap(gx0, a.s[2], a.N[2])), cc1 = int(fmap(gx1, a.s[2], a.N[2]));
+  const int cc0 = PK ? gx0 : int(fmap(gx0, a.s[2], a.N[2])), cc1 = PK ? gx1 : int(fmap(gx1, a.s[2], a.N[2]));
   const bool ccontig = cc1 == cc0 + 1;
+  const int pcx1 = gx1 - cidx(gx1);  // packed column of gx1 in a row coarse in y and z
   const int oc0 = a.out_full ? cc0 : gx0, oc1 = a.out_full ? cc1 : gx1;
   const bool ocontig = oc1 == oc0 + 1;
   // row blocks
   bool ay[RPW], oy1[RPW];
   TS way1[RPW], wby1[RPW];
-  int cr0[RPW], cr1[RPW];
+  int cr0[RPW], cr1[RPW], crc0[RPW], crc1[RPW];
   int64_t or0[RPW], or1[RPW];
 #pragma unroll
   for (int k = 0; k < RPW; ++k) {
@@ -609,14 +653,38 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     way1[k] = oy1[k] ? a.wa[1][g0 + 1] : TS(0);
     wby1[k] = oy1[k] ? a.wb[1][g0 + 1] : TS(0);
     const int g1 = min(g0 + 1, ny - 1);
-    cr0[k] = int(fmap(g0, a.s[1], a.N[1]) * a.y_sy);
-    cr1[k] = int(fmap(g1, a.s[1], a.N[1]) * a.y_sy);
+    cr0[k] = PK ? g0 * nx : int(fmap(g0, a.s[1], a.N[1]) * a.y_sy);
+    cr1[k] = PK ? g1 * nx : int(fmap(g1, a.s[1], a.N[1]) * a.y_sy);
+    // packed rows of a coarse plane
+    crc0[k] = g0 * nx - cidx(g0) * mx;
+    crc1[k] = g1 * nx - cidx(g1) * mx;
     or0[k] = (a.out_full ? fmap(g0, a.s[1], a.N[1]) : int64_t(g0)) * a.o_sy;
     or1[k] = (a.out_full ? fmap(g1, a.s[1], a.N[1]) : int64_t(g1)) * a.o_sy;
   }
 
   auto has_fine = [&](int t) { return t > qz0 && pidx(t, nz) - pidx(t - 1, nz) == 2; };
-  auto load_c = [&](TD* sb, int gz) {
+  // zc: gz is a coarse plane
+  auto load_c = [&](TD* sb, int gz, bool zc) {
+    if (cz) return;
+    if constexpr (PK) {
+      const TD* base = cin + int64_t(gz) * a.y_sz - int64_t(cidx(gz)) * a.c_sz;
+#pragma unroll
+      for (int k = 0; k < RPW; ++k) {
+        const int r0 = 2 * (warp * RPW + k);
+        if (!ay[k]) continue;
+        if (zc) {
+          // the coarse row g0 of a coarse plane holds its fine column only
+          if (ox1) cp_async(sb + r0 * RC + 2 * lane + 1, base + crc0[k] + pcx1, int(sizeof(TD)));
+          if (oy1[k])
+            load_pair(sb + (r0 + 1) * RC + 2 * lane, base + crc1[k] + cc0, base + crc1[k] + cc1, ax, ox1, true);
+        } else {
+          load_pair(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, true);
+          if (oy1[k])
+            load_pair(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, true);
+        }
+      }
+      return;
+    }
     const TD* base = cin + fmap(gz, a.s[0], a.N[0]) * a.y_sz;
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
@@ -636,9 +704,19 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
       if (cix < tcols) cp_async(tb + r * TC + cix, src + int64_t(r) * a.c_sy + cix, int(sizeof(TW)));
     }
     TD* sb = stage + st * 2 * RR * RC;
-    if (t < qz1) load_c(sb, pidx(t, nz));
-    if (has_fine(t)) load_c(sb + RR * RC, pidx(t, nz) - 1);
+    if (t < qz1) load_c(sb, pidx(t, nz), true);
+    if (has_fine(t)) load_c(sb + RR * RC, pidx(t, nz) - 1, false);
     cp_commit();
+  };
+
+  auto ldc = [&](const TD* p) -> TD2 {
+    TD2 v;
+    if (cz) {
+      v.x = v.y = TD(0);
+    } else {
+      v = *reinterpret_cast<const TD2*>(p);
+    }
+    return v;
   };
 
   TS Ip[RPW][4], In[RPW][4];
@@ -688,20 +766,20 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
         In[k][3] = TS(0);
       }
       if (act && own_c) {
-        const TD2 c0 = *reinterpret_cast<const TD2*>(sc + r0 * RC + 2 * lane);
+        const TD2 c0 = ldc(sc + r0 * RC + 2 * lane);
         store_pair<TO>(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(TS(c0.y) + In[k][1]), true, ox1, ocontig);
         if (oy1[k]) {
-          const TD2 c1 = *reinterpret_cast<const TD2*>(sc + (r0 + 1) * RC + 2 * lane);
+          const TD2 c1 = ldc(sc + (r0 + 1) * RC + 2 * lane);
           store_pair<TO>(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(TS(c1.x) + In[k][2]), TO(TS(c1.y) + In[k][3]),
                          true, ox1, ocontig);
         }
       }
       if (act && hf) {
-        const TD2 c0 = *reinterpret_cast<const TD2*>(sf + r0 * RC + 2 * lane);
+        const TD2 c0 = ldc(sf + r0 * RC + 2 * lane);
         store_pair<TO>(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
                        TO(TS(c0.y) + za * Ip[k][1] + zb * In[k][1]), true, ox1, ocontig);
         if (oy1[k]) {
-          const TD2 c1 = *reinterpret_cast<const TD2*>(sf + (r0 + 1) * RC + 2 * lane);
+          const TD2 c1 = ldc(sf + (r0 + 1) * RC + 2 * lane);
           store_pair<TO>(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
                          TO(TS(c1.y) + za * Ip[k][3] + zb * In[k][3]), true, ox1, ocontig);
         }
@@ -713,8 +791,8 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
   }
 }
 
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK>
 __global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  interp_body<NW, RPW, TD, TO, TS, TW>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  interp_body<NW, RPW, TD, TO, TS, TW, PK>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }

@@ -97,6 +97,11 @@ int build_plan_tables(mgr_plan* p) {
     }
     p->coarsest[a] = n;
   }
+  // class sizes: the coarsest grid, then |N_l| - |N_{l-1}| per level
+  p->class_off.assign(L + 2, 0);
+  p->class_off[1] = p->coarsest[0] * p->coarsest[1] * p->coarsest[2];
+  for (int l = 1; l <= L; ++l)
+    p->class_off[l + 1] = p->class_off[l] + p->geom[l].fine_count() - p->geom[l].coarse_count();
   auto push = [&](size_t count) {
     int64_t off = int64_t(T.size());
     // keep every table 16-byte aligned in both FP64 and FP32 copies
