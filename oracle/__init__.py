@@ -46,6 +46,8 @@ def _load():
         lib.oracle_pack_classes.restype = ctypes.c_int
         lib.oracle_unpack_classes.argtypes = [ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.oracle_unpack_classes.restype = ctypes.c_int
+        lib.oracle_quant_bins.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(dp), ctypes.c_int, ctypes.c_double, dp]
+        lib.oracle_quant_bins.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -194,9 +196,58 @@ def recompose_classes(packed, shape, nclasses=None, coords=None, levels=-1):
     return recompose(unpack_classes(packed, shape, nclasses, levels), coords, levels)
 
 
+def quant_bins(shape, tau, coords=None, levels=-1):
+    """Bin width of every coefficient class (length L+1) for the L-infinity tolerance ``tau``.
+
+    Reading of the quantization stage of Sec. V (the paper does not state the
+    quantizer): q_0 = 2 tau/(L+1), q_l = 2 tau/((L+1)(1 + |Z_l|_inf)) with Z_l the
+    level-l correction operator, which bounds the recomposed field's error by tau."""
+    lib = _load()
+    carr, keep = _coords_arg(shape, coords)
+    out = np.empty(64)
+    r = lib.oracle_quant_bins(len(shape), _shape_arr(shape), carr, int(levels), float(tau), _dptr(out))
+    del keep
+    if r < 0:
+        raise ValueError(f"quant_bins: invalid arguments ({r})")
+    return out[:r].copy()
+
+
+INT32_LIMIT = 2147483647
+
+
+def quantize(packed, bins, offsets, precision=np.float64):
+    """Codes of a class-packed coefficient array: k = round_half_even(c * (1/q_class)).
+
+    The rounding decision is taken in ``precision`` (the arithmetic type of the
+    coefficients); |k| is capped at 2^31-1.  Returns (int64 codes, saturated count)."""
+    c = np.asarray(packed).astype(precision)
+    codes = np.empty(c.shape, dtype=np.int64)
+    sat = 0
+    for l in range(len(bins)):
+        a, b = int(offsets[l]), int(offsets[l + 1])
+        qinv = precision(1.0 / float(bins[l]))
+        r = np.rint(c[a:b] * qinv)
+        bad = ~(np.abs(r) < precision(2147483648.0))
+        sat += int(bad.sum())
+        r = np.where(bad, np.where(r > 0, INT32_LIMIT, -INT32_LIMIT), r)
+        codes[a:b] = r.astype(np.int64)
+    return codes, sat
+
+
+def dequantize(codes, bins, offsets):
+    """Class-packed coefficient values k * q_class (FP64)."""
+    k = np.asarray(codes, dtype=np.float64)
+    out = np.empty(k.shape)
+    for l in range(len(bins)):
+        a, b = int(offsets[l]), int(offsets[l + 1])
+        out[a:b] = k[a:b] * float(bins[l])
+    return out
+
+
 def library_path():
     return _build.build()
 
 
 __all__ = ["max_levels", "default_levels", "decompose", "recompose", "mass_1d", "transfer_1d", "interp_1d",
-           "class_offsets", "pack_classes", "unpack_classes", "recompose_classes"]
+           "class_offsets", "pack_classes", "unpack_classes", "recompose_classes", "quant_bins", "quantize",
+           "dequantize"]

@@ -722,3 +722,73 @@ int oracle_unpack_classes(int ndim, const int64_t* shape, int levels, int nclass
   copy_args a = {packed, nodal, nclasses};
   return for_each_class_entry(ndim, shape, levels, unpack_one, &a);
 }
+
+/* ------------------------------------------------------------------ */
+/* Linear quantization bins with an L-infinity guarantee                */
+/* (the quantization stage that follows refactoring in the lossy        */
+/* compression workflow of Sec. V "Lossy compression")                  */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper moves quantization and dequantization to the GPU but does not
+ * state the quantizer.  Reading adopted: uniform (linear) quantization of
+ * each coefficient class with its own bin width q_l, codes k = round(c / q_l),
+ * dequantized values k * q_l, and widths chosen so that the recomposed field
+ * is within tau of the original in the maximum norm.
+ *
+ * Bound.  Recomposition maps coefficient perturbations d_0 (coarsest values)
+ * and d_l (level l) to a field perturbation e with e_0 = d_0 and
+ * e_l = d_l + P_l (e_{l-1} - Z_l d_l), where Z_l = (x_k M^c_k)^-1 (x_k K_k) is
+ * the correction operator of level l and P_l the interpolation (rows are
+ * convex weights, so |P_l|_inf = 1).  Hence
+ *   |e_L|_inf <= |d_0|_inf + sum_l (1 + |Z_l|_inf) |d_l|_inf,
+ * and |Z_l|_inf is the product over dimensions of the 1D norms (the infinity
+ * norm of a Kronecker product is the product of the norms).  Rounding gives
+ * |d_l|_inf <= q_l / 2; splitting tau equally over the L+1 classes gives
+ *   q_0 = 2 tau / (L+1),   q_l = 2 tau / ((L+1) (1 + |Z_l|_inf)).
+ */
+
+/* |Z|_inf of one dimension at one level: Z = (M^c)^-1 K, column by column. */
+static int correction_norm_1d(const level1d* o, double* norm) {
+  int64_t n = o->n, m = o->m;
+  double* col = (double*)malloc(sizeof(double) * m);
+  double* work = (double*)malloc(sizeof(double) * 2 * m);
+  double* rows = (double*)calloc((size_t)m, sizeof(double));
+  if (!col || !work || !rows) { free(col); free(work); free(rows); return -2; }
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t r = 0; r < m; ++r) col[r] = o->K[r * n + j];
+    line_thomas(o, col, work);
+    for (int64_t r = 0; r < m; ++r) rows[r] += col[r] < 0 ? -col[r] : col[r];
+  }
+  double best = 0.0;
+  for (int64_t r = 0; r < m; ++r)
+    if (rows[r] > best) best = rows[r];
+  *norm = best;
+  free(col); free(work); free(rows);
+  return 0;
+}
+
+/* bins[c] = bin width of class c (c = 0..L) for the L-infinity tolerance tau.
+   Returns L+1, or a negative error. */
+int oracle_quant_bins(int ndim, const int64_t* shape, const double* const* coords, int levels, double tau,
+                      double* bins) {
+  if (!(tau > 0.0)) return -1;
+  hierarchy h;
+  int rc = hierarchy_build(&h, ndim, shape, coords, levels);
+  if (rc != 0) return rc;
+  int L = h.L;
+  bins[0] = 2.0 * tau / (L + 1);
+  for (int l = 1; l <= L && rc == 0; ++l) {
+    level1d ops[ORACLE_MAXDIM];
+    if ((rc = build_level_ops(&h, l, ops)) != 0) break;
+    double znorm = 1.0;
+    for (int k = 0; k < ndim && rc == 0; ++k) {
+      double nk = 0.0;
+      rc = correction_norm_1d(&ops[k], &nk);
+      znorm *= nk;
+    }
+    bins[l] = 2.0 * tau / ((L + 1) * (1.0 + znorm));
+    for (int k = 0; k < ndim; ++k) level1d_free(&ops[k]);
+  }
+  hierarchy_free(&h);
+  return rc == 0 ? L + 1 : rc;
+}
