@@ -182,6 +182,48 @@ int mgr_recompose_packed(const mgr_plan* plan, const void* in, int nclasses, voi
 int mgr_pack_classes(const mgr_plan* plan, const void* nodal, void* packed, mgr_stream_t stream);
 int mgr_unpack_classes(const mgr_plan* plan, const void* packed, int nclasses, void* nodal, mgr_stream_t stream);
 
+/* ------------------------------------------------ linear quantization */
+
+/* The quantization stage that follows refactoring in a lossy compressor
+   (Sec. V "Lossy compression": refactoring, quantization and entropy coding;
+   quantization and dequantization run on the GPU next to the refactoring).
+   The paper does not state the quantizer; this library uses uniform bins per
+   coefficient class with widths chosen so that the recomposed field is
+   within `tau` of the input in the maximum norm:
+     q_0 = 2 tau / (L+1),  q_l = 2 tau / ((L+1) (1 + |Z_l|_inf)),
+   Z_l the level-l correction operator (x_k M_{l-1,k})^-1 (x_k P_k^T M_k).
+   (A perturbation d_l of class l reaches the field through
+   e_l = d_l + P_l (e_{l-1} - Z_l d_l) with |P_l|_inf = 1, and rounding to
+   the nearest code gives |d_l| <= q_l / 2.)  Codes are int32,
+   k = round-half-even(c * (1/q)) with the product and the rounding in the
+   stencil precision of the plan (FP64 for MGR_F64, FP32 for the FP32 forms;
+   class 0 in the solve precision), in the class-packed layout. */
+
+/* bins[c] = bin width of class c for tolerance tau > 0 (writes min(cap, L+1)
+   entries).  Host-only; the first call on a plan evaluates the operator
+   norms (O(n_k^2) per axis and level). */
+int mgr_quant_bins(const mgr_plan* plan, double tau, double* bins, int cap);
+
+/* Decompose and quantize in the same pass: the level pass writes the int32
+   code of each coefficient to its class-packed position (no coefficient
+   array is written).
+     codes      DEVICE, prod(shape) int32, not overlapping `in`
+     tau        max-norm tolerance of the recomposed field, > 0
+     saturated  DEVICE counter or NULL: the call adds the number of values
+                whose code does not fit in int32 (they are stored as
+                +-(2^31-1), and the tolerance no longer holds); zero it first
+   Workspace and stream as for mgr_decompose. */
+int mgr_decompose_quantized(const mgr_plan* plan, const void* in, int32_t* codes, double tau, void* workspace,
+                            unsigned long long* saturated, mgr_stream_t stream);
+
+/* Dequantize and recompose from classes 0..nclasses-1 of quantized codes
+   (nclasses = L+1: every class; the error is then at most tau plus
+   rounding).  Codes are read and scaled inside the level kernels.  Only the
+   first offsets[nclasses] codes are read.  `out`: DEVICE field, not
+   overlapping the codes. */
+int mgr_recompose_dequantized(const mgr_plan* plan, const int32_t* codes, int nclasses, double tau, void* out,
+                              void* workspace, mgr_stream_t stream);
+
 /* ------------------------------------------------------------ no-alloc form */
 
 /* Size of the fixed device scratch area used by mgr_decompose_noalloc. */

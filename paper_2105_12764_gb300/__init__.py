@@ -117,6 +117,9 @@ EXPORTED = {
     "mgr_recompose_packed": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "mgr_pack_classes": (_i, [_vp, _vp, _vp, _vp]),
     "mgr_unpack_classes": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "mgr_quant_bins": (_i, [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _i]),
+    "mgr_decompose_quantized": (_i, [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    "mgr_recompose_dequantized": (_i, [_vp, _vp, _i, ctypes.c_double, _vp, _vp, _vp]),
     "mgr_batch_submit": (_i, [_vp, ctypes.POINTER(mgr_request), _i, ctypes.POINTER(ctypes.c_uint64)]),
     "mgr_batch_poll": (_i, [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(_i)]),
     "mgr_batch_tuning": (_i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -303,6 +306,21 @@ class Plan:
     def unpack_classes(self, packed, nclasses, nodal, stream=None):
         _check("mgr_unpack_classes", lib.mgr_unpack_classes(self.handle, _ptr(packed), int(nclasses), _ptr(nodal),
                                                             _stream(stream)))
+
+    def quant_bins(self, tau):
+        """mgr_quant_bins: bin width of every class (L+1 entries) for the max-norm tolerance tau."""
+        arr = (ctypes.c_double * (self.levels + 1))()
+        _check("mgr_quant_bins", lib.mgr_quant_bins(self.handle, float(tau), arr, self.levels + 1))
+        return list(arr)
+
+    def decompose_quantized(self, inp, codes, tau, workspace, saturated=None, stream=None):
+        """mgr_decompose_quantized: int32 codes (class-packed) of the decomposition of `inp`."""
+        _check("mgr_decompose_quantized", lib.mgr_decompose_quantized(
+            self.handle, _ptr(inp), _ptr(codes), float(tau), _ptr(workspace), _ptr(saturated), _stream(stream)))
+
+    def recompose_dequantized(self, codes, nclasses, tau, out, workspace, stream=None):
+        _check("mgr_recompose_dequantized", lib.mgr_recompose_dequantized(
+            self.handle, _ptr(codes), int(nclasses), float(tau), _ptr(out), _ptr(workspace), _stream(stream)))
 
     def decompose_host(self, host_in, host_out, dev_in, dev_out, workspace, stream=None):
         _check("mgr_decompose_host", lib.mgr_decompose_host(self.handle, _ptr(host_in), _ptr(host_out), _ptr(dev_in),

@@ -29,9 +29,15 @@ int check_sticky() {
   return MGR_OK;
 }
 
-// Operation codes of run_op / the graph cache; OP_REC_PACKED carries the
-// number of classes in bits 8 and up.
-enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3 };
+// Operation codes of run_op / the graph cache; OP_REC_PACKED and OP_REC_DEQ
+// carry the number of classes in bits 8 and up.
+enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3, OP_DEC_QUANT = 4, OP_REC_DEQ = 5 };
+
+// Arguments of the quantized operations (part of the graph-cache key).
+struct Extra {
+  double tau = 0.0;
+  unsigned long long* sat = nullptr;
+};
 
 int check_op_args(const mgr_plan* p, const void* in, const void* out, const void* ws, bool alias_ok = true) {
   if (!p || !in || !out) return MGR_EINVAL;
@@ -45,40 +51,63 @@ int check_op_args(const mgr_plan* p, const void* in, const void* out, const void
   return MGR_OK;
 }
 
-cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st) {
+cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st,
+                    const Extra& x = Extra{}) {
+  std::vector<double> bins;
+  if ((op & 0xff) >= OP_DEC_QUANT && mgr::quant_bins(const_cast<mgr_plan*>(p), x.tau, bins) != MGR_OK)
+    return cudaErrorInvalidValue;
   switch (op & 0xff) {
     case OP_DEC: return mgr::enqueue_decompose(p, in, out, ws, st);
     case OP_REC: return mgr::enqueue_recompose(p, in, out, ws, st);
     case OP_DEC_PACKED: return mgr::enqueue_decompose_packed(p, in, out, ws, st);
-    default: return mgr::enqueue_recompose_packed(p, in, op >> 8, out, ws, st);
+    case OP_REC_PACKED: return mgr::enqueue_recompose_packed(p, in, op >> 8, out, ws, st);
+    case OP_DEC_QUANT: return mgr::enqueue_decompose_quantized(p, in, static_cast<int*>(out), bins.data(), x.sat, ws, st);
+    default: return mgr::enqueue_recompose_dequantized(p, static_cast<const int*>(in), op >> 8, bins.data(), out, ws, st);
   }
 }
 
-bool packed_op(int op) { return (op & 0xff) == OP_DEC_PACKED || (op & 0xff) == OP_REC_PACKED; }
+bool packed_op(int op) { return (op & 0xff) >= OP_DEC_PACKED; }
+
+// Arguments of a quantized operation: the field (elem bytes per element) and
+// the int32 codes must be aligned and must not overlap.
+int check_quant_args(const mgr_plan* p, const void* field, const void* codes, const void* ws, double tau) {
+  if (!p || !field || !codes || !(tau > 0.0)) return MGR_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(field) % p->elem) || (reinterpret_cast<uintptr_t>(codes) % 4)) return MGR_EINVAL;
+  const size_t fb = size_t(p->count) * p->elem, cb = size_t(p->count) * 4;
+  if (ranges_overlap(field, fb, codes, cb)) return MGR_EINVAL;
+  if (p->ws_bytes > 0) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign)) return MGR_EINVAL;
+    if (ranges_overlap(ws, p->ws_bytes, field, fb) || ranges_overlap(ws, p->ws_bytes, codes, cb)) return MGR_EINVAL;
+  }
+  return MGR_OK;
+}
 
 // Launch through a cached CUDA graph of the plan's launch sequence.  When the
 // caller's stream is itself being captured the kernels are enqueued directly
 // (they become part of the caller's graph).
-int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cudaStream_t st) {
+int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cudaStream_t st,
+           const Extra& x = Extra{}) {
   mgr_plan* p = const_cast<mgr_plan*>(cp);
-  int rc = check_op_args(p, in, out, ws, !packed_op(op));
+  int rc = (op & 0xff) == OP_DEC_QUANT  ? check_quant_args(p, in, out, ws, x.tau)
+           : (op & 0xff) == OP_REC_DEQ ? check_quant_args(p, out, in, ws, x.tau)
+                                        : check_op_args(p, in, out, ws, !packed_op(op));
   if (rc != MGR_OK) return rc;
   if ((rc = check_sticky()) != MGR_OK) return rc;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
-  if (cap != cudaStreamCaptureStatusNone) return enqueue(p, op, in, out, ws, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return enqueue(p, op, in, out, ws, st, x) == cudaSuccess ? MGR_OK : MGR_ECUDA;
 
   std::lock_guard<std::mutex> lk(p->graph_mu);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : p->graphs)
-    if (g.op == op && g.in == in && g.out == out && g.ws == ws) exec = g.exec;
+    if (g.op == op && g.in == in && g.out == out && g.ws == ws && g.tau == x.tau && g.aux == x.sat) exec = g.exec;
   if (!exec) {
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MGR_ECUDA;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue(p, op, in, out, ws, cs);
+      cudaError_t e2 = enqueue(p, op, in, out, ws, cs, x);
       e = cudaStreamEndCapture(cs, &graph);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -93,7 +122,7 @@ int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cuda
       cudaGraphExecDestroy(p->graphs.front().exec);
       p->graphs.erase(p->graphs.begin());
     }
-    p->graphs.push_back({op, in, out, ws, exec});
+    p->graphs.push_back({op, in, out, ws, x.tau, x.sat, exec});
   }
   return cudaGraphLaunch(exec, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
 }
@@ -303,6 +332,36 @@ int mgr_recompose_packed(const mgr_plan* p, const void* in, int nclasses, void* 
                          mgr_stream_t stream) {
   if (!p || nclasses < 1 || nclasses > p->levels + 1) return MGR_EINVAL;
   return run_op(p, OP_REC_PACKED | (nclasses << 8), in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mgr_quant_bins(const mgr_plan* p, double tau, double* bins, int cap) {
+  if (!p || (cap > 0 && !bins)) return MGR_EINVAL;
+  std::vector<double> b;
+  int rc;
+  try {
+    rc = mgr::quant_bins(const_cast<mgr_plan*>(p), tau, b);
+  } catch (const std::bad_alloc&) {
+    return MGR_ENOMEM;
+  }
+  if (rc != MGR_OK) return rc;
+  for (int i = 0; i < std::min(cap, int(b.size())); ++i) bins[i] = b[i];
+  return MGR_OK;
+}
+
+int mgr_decompose_quantized(const mgr_plan* p, const void* in, int32_t* codes, double tau, void* ws,
+                            unsigned long long* saturated, mgr_stream_t stream) {
+  Extra x;
+  x.tau = tau;
+  x.sat = saturated;
+  return run_op(p, OP_DEC_QUANT, in, codes, ws, reinterpret_cast<cudaStream_t>(stream), x);
+}
+
+int mgr_recompose_dequantized(const mgr_plan* p, const int32_t* codes, int nclasses, double tau, void* out, void* ws,
+                              mgr_stream_t stream) {
+  if (!p || nclasses < 1 || nclasses > p->levels + 1) return MGR_EINVAL;
+  Extra x;
+  x.tau = tau;
+  return run_op(p, OP_REC_DEQ | (nclasses << 8), codes, out, ws, reinterpret_cast<cudaStream_t>(stream), x);
 }
 
 int mgr_decompose_host(const mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 
 #include "mgr_internal.h"
 
@@ -179,20 +180,22 @@ dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
   return dim3(gx, gy, gz);
 }
 
-template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK>
+template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
   using C = LevelCfg<TS>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
-  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK>;
+  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   dim3 grid = level_grid(p, a);
   kern<<<grid, C::NW * 32, sm, st>>>(a);
 }
 
 // c: nodal coefficients (PK false), the packed class of level l (PK true), or
-// null for a dropped class (all coefficients zero)
-template <typename TD, typename TO, typename TS, typename TW, bool PK>
-void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st) {
+// null for a dropped class (all coefficients zero); QZ: c holds codes of bin
+// width qs
+template <typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ = false>
+void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st,
+                   double qs = 1.0) {
   const LevelGeom& g = p->geom[l];
   const TS* T = table<TS>(p);
   InterpArgs<TS, TW> a{};
@@ -212,6 +215,7 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
   a.c_sy = g.ax[2].m;
   a.out = out;
   a.out_full = out_full;
+  a.qs = qs;
   a.o_sz = out_full ? a.y_sz : int64_t(g.ax[1].n) * g.ax[2].n;
   a.o_sy = out_full ? a.y_sy : int64_t(g.ax[2].n);
   constexpr int BY = kInterpNW * kInterpRPW;
@@ -220,7 +224,7 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
-  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK>;
+  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK, QZ>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
 }
@@ -311,15 +315,52 @@ cudaError_t coarsest_copy_launch(const mgr_plan* p, TD* y, TW* w, bool packed, i
   return e;
 }
 
+// Class 0 of a quantized decomposition: codes of the compact coarsest values
+// v (dir 1) or those values from their codes (dir 0), arithmetic and rounding
+// decision in TW.  v is the compact coarse workspace, or the field itself
+// when the hierarchy has no level (L = 0).
+template <typename TV, typename TW>
+__global__ void k_coarsest_q(int* codes, TV* v, int64_t total, double q, int dir, unsigned long long* sat) {
+  const TW qinv = TW(1.0 / q), qq = TW(q);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    if (dir)
+      codes[i] = quant_code(TW(v[i]), qinv, sat);
+    else
+      v[i] = TV(dequant(codes[i], qq));
+  }
+}
+
+template <typename TV, typename TW>
+cudaError_t coarsest_q_launch(const mgr_plan* p, int* codes, TV* v, double q, int dir, unsigned long long* sat,
+                              cudaStream_t st) {
+  const int64_t total = p->class_off[1];
+  rec_begin(st);
+  k_coarsest_q<TV, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(codes, v, total, q, dir, sat);
+  cudaError_t e = cudaGetLastError();
+  rec_end(st, "coarsest", 0, double(total) * (sizeof(int) + sizeof(TV)), 0.0);
+  return e;
+}
+
 // PK: write the coefficients in the class-packed layout (class l at
-// p->class_off[l]; `out` must not overlap `in`).
-template <typename TD, typename TS, typename TW, bool PK>
-cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+// p->class_off[l]; `out` must not overlap `in`).  QZ (with PK): write int32
+// codes with the bin widths bins[0..L] instead, counting saturated codes in
+// *sat (when not null).
+template <typename TD, typename TS, typename TW, bool PK, bool QZ = false>
+cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st,
+                        const double* bins = nullptr, unsigned long long* sat = nullptr) {
+  static_assert(PK || !QZ, "quantized output is class-packed");
+  using TY = std::conditional_t<QZ, int, TD>;  // coefficient output type
   const int L = p->levels;
   const size_t bytes = size_t(p->count) * sizeof(TD);
   if (L == 0) {
-    if (in != out) return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
-    return cudaSuccess;
+    // the whole field is the coarsest class
+    if constexpr (QZ) {
+      return coarsest_q_launch<TD, TW>(p, static_cast<int*>(out), const_cast<TD*>(static_cast<const TD*>(in)),
+                                       bins[0], 1, sat, st);
+    } else {
+      if (in != out) return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
+      return cudaSuccess;
+    }
   }
   const bool inplace = !PK && (in == out);
   Bufs b = split_ws(p, ws);
@@ -331,9 +372,13 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     const LevelGeom& g = p->geom[l];
     a.y = out;
     if (PK) {
-      a.y = static_cast<TD*>(out) + p->class_off[l];
+      a.y = static_cast<TY*>(out) + p->class_off[l];
       a.y_sz = int64_t(g.ax[1].n) * g.ax[2].n;
       a.y_sy = g.ax[2].n;
+    }
+    if (QZ) {
+      a.qs = 1.0 / bins[l];
+      a.qsat = sat;
     }
     a.w = nxt;
     a.f = F;
@@ -344,13 +389,13 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
       a.in_full = 1;
       a.in_sz = p->full[1] * p->full[2];
       a.in_sy = p->full[2];
-      launch_level<0, TD, TD, TS, TW, PK>(p, a, st);
+      launch_level<0, TD, TY, TS, TW, PK, QZ>(p, a, st);
     } else {
       a.in = cur;
       a.in_full = 0;
       a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
       a.in_sy = g.ax[2].n;
-      launch_level<0, TW, TD, TS, TW, PK>(p, a, st);
+      launch_level<0, TW, TY, TS, TW, PK, QZ>(p, a, st);
     }
     cudaError_t e = cudaGetLastError();
     {
@@ -377,46 +422,60 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     cur = nxt;
   }
   // coarsest values into their nodal positions / class 0
-  return coarsest_copy_launch<TD, TW>(p, static_cast<TD*>(out), cur, PK, 1, st);
+  if constexpr (QZ) return coarsest_q_launch<TW, TW>(p, static_cast<int*>(out), cur, bins[0], 1, sat, st);
+  else return coarsest_copy_launch<TD, TW>(p, static_cast<TD*>(out), cur, PK, 1, st);
 }
 
 // Recompose from classes 0..ncls-1 (ncls = L+1: all of them).  Levels whose
 // class is dropped have zero coefficients, hence a zero correction: they are
 // interpolation only.  PK: `in` is class-packed (its first class_off[ncls]
 // elements are read) and must not overlap `out`.
-template <typename TD, typename TS, typename TW, bool PK>
-cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st, int ncls) {
+// QZ (with PK): `in` holds int32 codes with the bin widths bins[0..L].
+template <typename TD, typename TS, typename TW, bool PK, bool QZ = false>
+cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st, int ncls,
+                        const double* bins = nullptr) {
+  static_assert(PK || !QZ, "quantized input is class-packed");
+  using TY = std::conditional_t<QZ, int, TD>;  // coefficient input type
   const int L = p->levels;
   const size_t bytes = size_t(p->count) * sizeof(TD);
   if (L == 0) {
-    if (in != out) return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
-    return cudaSuccess;
+    if constexpr (QZ) {
+      return coarsest_q_launch<TD, TW>(p, const_cast<int*>(static_cast<const int*>(in)), static_cast<TD*>(out),
+                                       bins[0], 0, nullptr, st);
+    } else {
+      if (in != out) return cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
+      return cudaSuccess;
+    }
   }
   Bufs b = split_ws(p, ws);
   TW* F = static_cast<TW*>(b.F);
   // coarsest grid from the nodal positions / class 0
   TW* cur = static_cast<TW*>((L % 2 == 1) ? b.A : b.B);  // level 0 lives where decompose left it
   {
-    cudaError_t e = coarsest_copy_launch<TD, TW>(p, const_cast<TD*>(static_cast<const TD*>(in)), cur, PK, 0, st);
+    cudaError_t e;
+    if constexpr (QZ) e = coarsest_q_launch<TW, TW>(p, const_cast<int*>(static_cast<const int*>(in)), cur, bins[0], 0,
+                                                    nullptr, st);
+    else e = coarsest_copy_launch<TD, TW>(p, const_cast<TD*>(static_cast<const TD*>(in)), cur, PK, 0, st);
     if (e != cudaSuccess) return e;
   }
   for (int l = 1; l <= L; ++l) {
     const LevelGeom& g = p->geom[l];
-    const void* cl = PK ? static_cast<const void*>(static_cast<const TD*>(in) + p->class_off[l]) : in;
+    const void* cl = PK ? static_cast<const void*>(static_cast<const TY*>(in) + p->class_off[l]) : in;
+    const double qs = QZ ? bins[l] : 1.0;
     if (l >= ncls) {
       // dropped class: v = interpolant of the coarse values
       rec_begin(st);
       if (l == L) {
-        launch_interp<TD, TD, TS, TW, PK>(p, l, nullptr, cur, out, 1, st);
+        launch_interp<TY, TD, TS, TW, PK, QZ>(p, l, nullptr, cur, out, 1, st, qs);
       } else {
         TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
-        launch_interp<TD, TW, TS, TW, PK>(p, l, nullptr, cur, nxt, 0, st);
+        launch_interp<TY, TW, TS, TW, PK, QZ>(p, l, nullptr, cur, nxt, 0, st, qs);
         cur = nxt;
       }
       cudaError_t e = cudaGetLastError();
       {
         const Work wk = work_interp(p, l);
-        rec_end(st, "interp_zero", l, wk.bytes - double(g.fine_count()) * sizeof(TD), wk.flops);
+        rec_end(st, "interp_zero", l, wk.bytes - double(g.fine_count()) * p->elem, wk.flops);
       }
       if (e != cudaSuccess) return e;
       continue;
@@ -436,8 +495,9 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     a.w = nullptr;
     a.y = nullptr;
     a.write_y = 0;
+    a.qs = qs;
     rec_begin(st);
-    launch_level<1, TD, TD, TS, TW, PK>(p, a, st);
+    launch_level<1, TY, TY, TS, TW, PK, QZ>(p, a, st);
     cudaError_t e = cudaGetLastError();
     {
       const Work wk = work_level_load(p, l, false);
@@ -447,10 +507,10 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if ((e = solve_level<TW>(p, l, F, cur, SOLVE_SUB, st)) != cudaSuccess) return e;
     rec_begin(st);
     if (l == L) {
-      launch_interp<TD, TD, TS, TW, PK>(p, l, cl, cur, out, 1, st);
+      launch_interp<TY, TD, TS, TW, PK, QZ>(p, l, cl, cur, out, 1, st, qs);
     } else {
       TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
-      launch_interp<TD, TW, TS, TW, PK>(p, l, cl, cur, nxt, 0, st);
+      launch_interp<TY, TW, TS, TW, PK, QZ>(p, l, cl, cur, nxt, 0, st, qs);
       cur = nxt;
     }
     e = cudaGetLastError();
@@ -496,6 +556,24 @@ cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls
     case kFormF64: return recompose_t<double, double, double, true>(p, in, out, ws, st, ncls);
     case kFormF32: return recompose_t<float, float, float, true>(p, in, out, ws, st, ncls);
     default: return recompose_t<float, float, double, true>(p, in, out, ws, st, ncls);
+  }
+}
+
+cudaError_t enqueue_decompose_quantized(const mgr_plan* p, const void* in, int* codes, const double* bins,
+                                        unsigned long long* sat, void* ws, cudaStream_t st) {
+  switch (p->form) {
+    case kFormF64: return decompose_t<double, double, double, true, true>(p, in, codes, ws, st, bins, sat);
+    case kFormF32: return decompose_t<float, float, float, true, true>(p, in, codes, ws, st, bins, sat);
+    default: return decompose_t<float, float, double, true, true>(p, in, codes, ws, st, bins, sat);
+  }
+}
+
+cudaError_t enqueue_recompose_dequantized(const mgr_plan* p, const int* codes, int ncls, const double* bins,
+                                          void* out, void* ws, cudaStream_t st) {
+  switch (p->form) {
+    case kFormF64: return recompose_t<double, double, double, true, true>(p, codes, out, ws, st, ncls, bins);
+    case kFormF32: return recompose_t<float, float, float, true, true>(p, codes, out, ws, st, ncls, bins);
+    default: return recompose_t<float, float, double, true, true>(p, codes, out, ws, st, ncls, bins);
   }
 }
 

@@ -81,6 +81,10 @@ struct mgr_plan {
   // class-packed layout: class c (0 = coarsest grid, l = coefficients of level
   // l) starts at class_off[c]; class_off[L+1] = count
   std::vector<int64_t> class_off;
+  // quantization: |Z_l|_inf of each level's correction operator (built on
+  // first use, under quant_mu)
+  std::mutex quant_mu;
+  std::vector<double> znorm;
   mgr::Tables tables;
   // workspace layout (bytes)
   size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_bytes = 0;
@@ -91,6 +95,8 @@ struct mgr_plan {
     const void* in;
     void* out;
     void* ws;
+    double tau;   // quantized operations: tolerance
+    void* aux;    // quantized decomposition: saturation counter
     cudaGraphExec_t exec;
   };
   std::vector<GraphEntry> graphs;
@@ -136,6 +142,13 @@ cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void
 cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,
                                      cudaStream_t st);
+// quantized class-packed forms: int32 codes with bin widths bins[0..L]
+cudaError_t enqueue_decompose_quantized(const mgr_plan* p, const void* in, int* codes, const double* bins,
+                                        unsigned long long* sat, void* ws, cudaStream_t st);
+cudaError_t enqueue_recompose_dequantized(const mgr_plan* p, const int* codes, int ncls, const double* bins,
+                                          void* out, void* ws, cudaStream_t st);
+// mgr_plan.cpp: bin widths for the max-norm tolerance tau (L+1 entries)
+int quant_bins(mgr_plan* p, double tau, std::vector<double>& bins);
 // mgr_classes.cu: layout conversion nodal <-> class-packed
 cudaError_t enqueue_pack_classes(const mgr_plan* p, const void* nodal, void* packed, cudaStream_t st);
 cudaError_t enqueue_unpack_classes(const mgr_plan* p, const void* packed, int ncls, void* nodal, cudaStream_t st);

@@ -36,6 +36,11 @@
 //   i*n1*n2 - cb(i)*m1*m2 + (i fine ? j*n2 + k
 //                                   : j*n2 - cb(j)*m2 + (j fine ? k : k - cb(k)))
 // from the class start, so plane and row offsets stay separable.
+//
+// Quantized coefficients (QZ, class-packed only): decomposition writes the
+// int32 code round_half_even(c * (1/q_l)) of each coefficient (the rounding
+// decision in the stencil type TS) and recomposition reads codes and uses
+// code * q_l; q_l is the bin width of the level's class.
 #pragma once
 
 template <int NW, int RPW>
@@ -72,6 +77,72 @@ template <>
 struct Pair<double> {
   using type = double2;
 };
+template <>
+struct Pair<int> {
+  using type = int2;
+};
+
+// int32 code of value v for 1/bin width qinv: v * qinv rounded to FP32 / FP64
+// (no contraction), then rounded half to even; values whose code does not fit
+// in (-2^31, 2^31) (and NaN) become +-(2^31-1) and are counted.
+__device__ __forceinline__ int quant_code(float v, float qinv, unsigned long long* sat) {
+  const float t = __fmul_rn(v, qinv);
+  const float r = rintf(t);
+  if (!(fabsf(r) < 2147483648.0f)) {
+    if (sat) atomicAdd(sat, 1ull);
+    return t > 0.0f ? 2147483647 : -2147483647;
+  }
+  return int(r);
+}
+// FP64: the product is the only FP64 operation; t is rounded to an integer
+// from its IEEE-754 fields with integer instructions (the FP64 pipe, which
+// bounds the FP64 level pass, has a small fraction of the integer pipes'
+// throughput).  With t = 1.m * 2^e and the 53-bit significand M = 1m,
+// |t| < 0.5 for e < -1; otherwise floor|t| = M >> (52 - e) and the
+// remainder decides round-half-to-even.
+__device__ __forceinline__ int quant_code(double v, double qinv, unsigned long long* sat) {
+  const double t = __dmul_rn(v, qinv);
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(t));
+  const int e = int((b >> 52) & 0x7ffu) - 1023;
+  if (e < -1) return 0;
+  const bool neg = (b >> 63) != 0;
+  if (e <= 30) {
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 52 - e;  // 22 .. 53
+    unsigned long long q = m >> sh;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    if (q < (1ull << 31)) return neg ? -int(q) : int(q);
+  }
+  if (sat) atomicAdd(sat, 1ull);
+  const bool nan = e == 1024 && (b & 0xFFFFFFFFFFFFFull) != 0;
+  return (!neg && !nan) ? 2147483647 : -2147483647;
+}
+
+// Code k as a value of the stencil type.  FP64 assembles the IEEE-754 fields
+// of the (exactly representable) integer with integer instructions: sign,
+// exponent 1023 + msb(|k|), and |k| shifted up to the 52-bit fraction.
+template <typename TS>
+__device__ __forceinline__ TS code_value(int k);
+template <>
+__device__ __forceinline__ float code_value<float>(int k) {
+  return float(k);
+}
+template <>
+__device__ __forceinline__ double code_value<double>(int k) {
+  const unsigned s = unsigned(k) & 0x80000000u;
+  const unsigned a = k < 0 ? 0u - unsigned(k) : unsigned(k);
+  const int e = 31 - __clz(a | 1u);
+  const unsigned long long m = (static_cast<unsigned long long>(a) << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  const unsigned long long bits =
+      (static_cast<unsigned long long>(s) << 32) | (static_cast<unsigned long long>(1023 + e) << 52) | m;
+  return k == 0 ? 0.0 : __longlong_as_double(static_cast<long long>(bits));
+}
+// Dequantized value k * q.
+template <typename TS>
+__device__ __forceinline__ TS dequant(int k, TS q) {
+  return code_value<TS>(k) * q;
+}
 
 template <typename TS, typename TW>
 struct LevelArgs {
@@ -90,6 +161,8 @@ struct LevelArgs {
   const TS* k[3];
   int qz_chunk;
   int write_y;
+  double qs;                // QZ: 1/bin width (MODE 0) or bin width (MODE 1)
+  unsigned long long* qsat; // QZ, MODE 0: saturated-code counter (may be null)
 };
 
 // FP64 keeps the x / y stencil weights in shared memory (the FP64 pass is
@@ -139,7 +212,10 @@ __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bo
 // with `smem_raw` the CTA's dynamic shared memory (level_smem_bytes).
 // PK: coefficients in the class-packed layout (MODE 0 writes `y`, MODE 1 reads
 // `in` as the class of this level; y_sz / in_sz = n1*n2, y_sy / in_sy = n2).
-template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK = false>
+// QZ (with PK): those coefficients are int32 codes (TD = int in MODE 0, TI =
+// int in MODE 1).
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK = false,
+          bool QZ = false>
 __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, int by, int bz,
                                            unsigned char* smem_raw) {
   using G = LevelTile<NW, RPW>;
@@ -171,6 +247,24 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const TI* __restrict__ in = static_cast<const TI*>(a.in);
   TD* __restrict__ yout = static_cast<TD*>(a.y);
   const bool wy = (MODE == 0) && a.write_y;
+  const TS qs = QZ ? TS(a.qs) : TS(1);
+  // value written for coefficient v when `st` (the node is stored: values of
+  // nodes that are not stored are never quantized, so never counted as
+  // saturated) (MODE 0); value of a read coefficient (MODE 1)
+  auto yval = [&](TS v, bool st) -> TD {
+    if constexpr (QZ) return st ? TD(quant_code(v, qs, a.qsat)) : TD(0);
+    else return TD(v);
+  };
+  // (MODE 1 with QZ: the code itself; the bin width scales the load vector
+  // once per coarse node instead, see fout)
+  auto cval = [&](TI v) -> TS {
+    if constexpr (QZ && MODE == 1) return code_value<TS>(int(v));
+    else return TS(v);
+  };
+  auto fout = [&](TS acc) -> TW {
+    if constexpr (QZ && MODE == 1) return TW(acc) * TW(a.qs);
+    else return TW(acc);
+  };
 
   // ---- per-lane column constants (in-plane offsets fit in 32 bits)
   const int cx0 = 2 * lane;
@@ -346,7 +440,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       rc[k][2] = p1.x;
       rc[k][3] = p1.y;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) vc[k][e] = TS(rc[k][e]);
+      for (int e = 0; e < 4; ++e) vc[k][e] = cval(rc[k][e]);
     }
     // ---- coarse-z plane: x interpolants of the coarse rows
     TS v12[RPW];
@@ -406,12 +500,12 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       if (PK && wy && own_c) {
         // packed class: the coarse row gy0 keeps only its fine column gx1
         const int r0 = yr0[k] - cidx(gy0[k]) * mx, r1 = yr1[k] - cidx(gy0[k] + 1) * mx;
-        if (owy0[k] && owx1 && fx1) yzc[r0 + pcx1] = TD(c[1]);
+        if (owy0[k] && owx1 && fx1) yzc[r0 + pcx1] = yval(c[1], true);
         if (owy1[k]) {
           if (fy1[k]) {
-            store_pair<TD>(yzc + r1 + yc0, yzc + r1 + yc1, TD(c[2]), TD(c[3]), owx0, owx1, true);
+            store_pair<TD>(yzc + r1 + yc0, yzc + r1 + yc1, yval(c[2], owx0), yval(c[3], owx1), owx0, owx1, true);
           } else if (owx1 && fx1) {
-            yzc[r1 + pcx1] = TD(c[3]);
+            yzc[r1 + pcx1] = yval(c[3], true);
           }
         }
       } else if (wy && own_c) {
@@ -437,10 +531,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         {
           const TI2 f0 = *reinterpret_cast<const TI2*>(sf + r0 * RC + cx0);
           const TI2 f1 = *reinterpret_cast<const TI2*>(sf + (r0 + 1) * RC + cx0);
-          vf[0] = TS(f0.x);
-          vf[1] = TS(f0.y);
-          vf[2] = TS(f1.x);
-          vf[3] = TS(f1.y);
+          vf[0] = cval(f0.x);
+          vf[1] = cval(f0.y);
+          vf[2] = cval(f1.x);
+          vf[3] = cval(f1.y);
         }
         TS d[4];
         if (MODE == 0) {
@@ -454,9 +548,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
         *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
         if (wy && own_f) {
-          store_pair<TD>(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, TD(d[0]), TD(d[1]), owy0[k] && owx0,
+          store_pair<TD>(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, yval(d[0], owy0[k] && owx0), yval(d[1], owy0[k] && owx1), owy0[k] && owx0,
                          owy0[k] && owx1, ycontig);
-          store_pair<TD>(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, TD(d[2]), TD(d[3]), owy1[k] && owx0,
+          store_pair<TD>(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, yval(d[2], owy1[k] && owx0), yval(d[3], owy1[k] && owx1), owy1[k] && owx0,
                          owy1[k] && owx1, ycontig);
         }
       }
@@ -552,7 +646,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           acc1[k] += wzf[1] * gf;
         }
         if (t - 1 >= qz0 && t - 1 < qz1)
-          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = TW(acc0[k]);
+          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
       }
       acc0[k] = acc1[k];
       acc1[k] = acc2[k];
@@ -565,15 +659,15 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int j = warp * RPW + k;
-      if (j < nby && kxo) a.f[int64_t(mz - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = TW(acc0[k]);
+      if (j < nby && kxo) a.f[int64_t(mz - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
     }
   }
 }
 
-template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK>
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -600,6 +694,7 @@ struct InterpArgs {
   const TS* wa[3];
   const TS* wb[3];
   int qz_chunk;
+  double qs;  // QZ: bin width of the level's class
 };
 
 template <int NW, int RPW, typename TD, typename TW>
@@ -608,7 +703,8 @@ constexpr size_t interp_smem_bytes() {
 }
 
 // PK: `c` is the class-packed class of this level (y_sz = n1*n2, y_sy = n2).
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK = false>
+// QZ (with PK): `c` holds int32 codes (TD = int), coefficient = code * qs.
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK = false, bool QZ = false>
 __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx, int by, int bz,
                                             unsigned char* smem_raw) {
   constexpr int BY = NW * RPW, TR = BY + 1, TC = 33, RR = 2 * BY, RC = 64;
@@ -624,6 +720,12 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
   const int tcols = min(TC, mx - qx0), trows = min(TR, my - qy0);
   const TD* __restrict__ cin = static_cast<const TD*>(a.c);
   const bool cz = cin == nullptr;  // coefficients of a dropped class: zero
+  const TS qs = QZ ? TS(a.qs) : TS(1);
+  // coefficient v plus interpolant b (QZ: code * q + b in one FMA)
+  auto cadd = [&](TD v, TS b) -> TS {
+    if constexpr (QZ) return fma(code_value<TS>(int(v)), qs, b);
+    else return TS(v) + b;
+  };
   TO* __restrict__ out = static_cast<TO*>(a.out);
 
   // column block of this lane: fine nodes p(qx) and, when a fine node lies
@@ -767,21 +869,21 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
       }
       if (act && own_c) {
         const TD2 c0 = ldc(sc + r0 * RC + 2 * lane);
-        store_pair<TO>(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(TS(c0.y) + In[k][1]), true, ox1, ocontig);
+        store_pair<TO>(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(cadd(c0.y, In[k][1])), true, ox1, ocontig);
         if (oy1[k]) {
           const TD2 c1 = ldc(sc + (r0 + 1) * RC + 2 * lane);
-          store_pair<TO>(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(TS(c1.x) + In[k][2]), TO(TS(c1.y) + In[k][3]),
+          store_pair<TO>(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(cadd(c1.x, In[k][2])), TO(cadd(c1.y, In[k][3])),
                          true, ox1, ocontig);
         }
       }
       if (act && hf) {
         const TD2 c0 = ldc(sf + r0 * RC + 2 * lane);
-        store_pair<TO>(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
-                       TO(TS(c0.y) + za * Ip[k][1] + zb * In[k][1]), true, ox1, ocontig);
+        store_pair<TO>(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(QZ ? cadd(c0.x, za * Ip[k][0] + zb * In[k][0]) : TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
+                       TO(QZ ? cadd(c0.y, za * Ip[k][1] + zb * In[k][1]) : TS(c0.y) + za * Ip[k][1] + zb * In[k][1]), true, ox1, ocontig);
         if (oy1[k]) {
           const TD2 c1 = ldc(sf + (r0 + 1) * RC + 2 * lane);
-          store_pair<TO>(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
-                         TO(TS(c1.y) + za * Ip[k][3] + zb * In[k][3]), true, ox1, ocontig);
+          store_pair<TO>(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(QZ ? cadd(c1.x, za * Ip[k][2] + zb * In[k][2]) : TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
+                         TO(QZ ? cadd(c1.y, za * Ip[k][3] + zb * In[k][3]) : TS(c1.y) + za * Ip[k][3] + zb * In[k][3]), true, ox1, ocontig);
         }
       }
 #pragma unroll
@@ -791,8 +893,8 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
   }
 }
 
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK>
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  interp_body<NW, RPW, TD, TO, TS, TW, PK>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  interp_body<NW, RPW, TD, TO, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }

@@ -15,6 +15,7 @@
 //     forward   y_q = f'_q - ta_q * y_{q-1},   ta_q = e_{q-1} / u_q
 //     backward  z_q = y_q  - tb_q * z_{q+1},   tb_q = e_q / u_q
 // where e_q = h_q / 6 is the off-diagonal of M_{l-1}.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -269,6 +270,63 @@ Work work_solve(const mgr_plan* p, int l, int axis, bool final_op) {
   w.bytes = 2.0 * m * sw + (final_op ? 2.0 * m * sw : 0.0);
   w.flops = 4.0 * m + (final_op ? m : 0.0);
   return w;
+}
+
+// ---------------------------------------------------------------------------
+// Quantization bins (the quantization stage around the refactoring, Sec. V).
+// A perturbation d_l of the level-l coefficients reaches the recomposed field
+// through e_l = d_l + P_l (e_{l-1} - Z_l d_l), Z_l = (x_k M_{l-1,k})^-1 (x_k K_k),
+// |P_l|_inf = 1, so |e_L|_inf <= |d_0| + sum_l (1 + |Z_l|_inf) |d_l|; with
+// rounding, |d_l| <= q_l/2, and tau split evenly over the L+1 classes:
+// q_0 = 2 tau/(L+1), q_l = 2 tau/((L+1)(1 + |Z_l|_inf)).  |Z_l|_inf is the
+// product over axes of the 1D norms, each evaluated exactly, column by
+// column, with this plan's scaled K rows and Thomas recurrences.
+// ---------------------------------------------------------------------------
+namespace {
+
+double correction_norm(const mgr_plan* p, int l, int a) {
+  const AxisLevel& ax = p->geom[l].ax[a];
+  if (!ax.active) return 1.0;
+  const int n = ax.n, m = ax.m;
+  const double* T = p->tables.host.data();
+  const double* K = T + ax.o_k;
+  const double* ta = T + ax.o_ta;
+  const double* tb = T + ax.o_tb;
+  std::vector<double> z(m), rows(m, 0.0);
+  for (int j = 0; j < n; ++j) {
+    std::fill(z.begin(), z.end(), 0.0);
+    for (int q = std::max(0, j / 2 - 2); q <= std::min(m - 1, j / 2 + 2); ++q) {
+      const int t = j - std::min(2 * q, n - 1) + 2;
+      if (t >= 0 && t <= 4) z[q] = K[5 * q + t];
+    }
+    for (int q = 1; q < m; ++q) z[q] -= ta[q] * z[q - 1];
+    for (int q = m - 2; q >= 0; --q) z[q] -= tb[q] * z[q + 1];
+    for (int q = 0; q < m; ++q) rows[q] += std::fabs(z[q]);
+  }
+  return *std::max_element(rows.begin(), rows.end());
+}
+
+}  // namespace
+
+int quant_bins(mgr_plan* p, double tau, std::vector<double>& bins) {
+  if (!(tau > 0.0) || !std::isfinite(tau)) return MGR_EINVAL;
+  const int L = p->levels;
+  {
+    std::lock_guard<std::mutex> lk(p->quant_mu);
+    if (int(p->znorm.size()) != L + 1) {
+      std::vector<double> zn(L + 1, 0.0);
+      for (int l = 1; l <= L; ++l) {
+        double v = 1.0;
+        for (int a = 0; a < kAxes; ++a) v *= correction_norm(p, l, a);
+        zn[l] = v;
+      }
+      p->znorm = zn;
+    }
+  }
+  bins.assign(L + 1, 0.0);
+  bins[0] = 2.0 * tau / (L + 1);
+  for (int l = 1; l <= L; ++l) bins[l] = 2.0 * tau / ((L + 1) * (1.0 + p->znorm[l]));
+  return MGR_OK;
 }
 
 Work work_interp(const mgr_plan* p, int l) {

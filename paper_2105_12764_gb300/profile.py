@@ -25,6 +25,7 @@ def main():
     ap.add_argument("--shape", default="513", help="n (cube) or n0,n1,n2")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--plain", action="store_true")
+    ap.add_argument("--packed", action="store_true", help="class-packed decompose / recompose")
     a = ap.parse_args()
     shape = tuple(int(v) for v in a.shape.split(","))
     if len(shape) == 1:
@@ -38,26 +39,35 @@ def main():
     x = torch.randn(shape, dtype=td, device="cuda", generator=g)
     y, z = torch.empty_like(x), torch.empty_like(x)
     ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    L = plan.levels
+    if a.packed:
+        dec = lambda: plan.decompose_packed(x, y, ws)  # noqa: E731
+        rec = lambda: plan.recompose_packed(y, L + 1, z, ws)  # noqa: E731
+        ops = ((mgr.MGR_OP_DECOMPOSE_PACKED, (x, y)), (mgr.MGR_OP_RECOMPOSE_PACKED, (y, z)))
+    else:
+        dec = lambda: plan.decompose(x, y, ws)  # noqa: E731
+        rec = lambda: plan.recompose(y, z, ws)  # noqa: E731
+        ops = ((0, (x, y)), (1, (y, z)))
     if a.plain:
         for _ in range(a.reps):
-            plan.decompose(x, y, ws)
-            plan.recompose(y, z, ws)
+            dec()
+            rec()
         torch.cuda.synchronize()
         print(f"done: round trip max error {float((z - x).abs().max()):.3e}")
         return
     for _ in range(2):
-        plan.decompose(x, y, ws)
-        plan.recompose(y, z, ws)
+        dec()
+        rec()
     torch.cuda.synchronize()
     agg = {}
     for _ in range(a.reps):
-        for op, (src, dst) in ((0, (x, y)), (1, (y, z))):
+        for op, (src, dst) in ops:
             for r in plan.profile(op, src, dst, ws):
                 e = agg.setdefault((r["name"], r["level"]), [0.0, 0, r["bytes"], r["flops"]])
                 e[0] += r["ms"]
                 e[1] += 1
     tot = sum(v[0] / v[1] for v in agg.values())
-    print(f"form {a.form} shape {shape} levels {plan.levels}: {tot:.3f} ms per decompose + recompose "
+    print(f"form {a.form}{' packed' if a.packed else ''} shape {shape} levels {plan.levels}: {tot:.3f} ms per decompose + recompose "
           f"(sum of event-bracketed launches)")
     for (name, lvl), v in sorted(agg.items(), key=lambda kv: -kv[1][0])[:24]:
         ms = v[0] / v[1]
@@ -66,10 +76,10 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record()
     for _ in range(a.reps):
-        plan.decompose(x, y, ws)
+        dec()
     ev[1].record()
     for _ in range(a.reps):
-        plan.recompose(y, z, ws)
+        rec()
     ev[2].record()
     torch.cuda.synchronize()
     print(f"graph-replayed: decompose {ev[0].elapsed_time(ev[1]) / a.reps:.3f} ms, "
