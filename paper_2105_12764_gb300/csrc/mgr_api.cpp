@@ -41,6 +41,7 @@ struct Extra {
 
 int check_op_args(const mgr_plan* p, const void* in, const void* out, const void* ws, bool alias_ok = true) {
   if (!p || !in || !out) return MGR_EINVAL;
+  if (p->desc.ndim == 4) alias_ok = false;  // the spatiotemporal form is out of place
   const size_t bytes = size_t(p->count) * p->elem;
   if ((reinterpret_cast<uintptr_t>(in) % p->elem) || (reinterpret_cast<uintptr_t>(out) % p->elem)) return MGR_EINVAL;
   if ((in != out || !alias_ok) && ranges_overlap(in, bytes, out, bytes)) return MGR_EINVAL;
@@ -88,6 +89,7 @@ int check_quant_args(const mgr_plan* p, const void* field, const void* codes, co
 int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cudaStream_t st,
            const Extra& x = Extra{}) {
   mgr_plan* p = const_cast<mgr_plan*>(cp);
+  if (p && p->desc.ndim == 4 && packed_op(op)) return MGR_EINVAL;  // 4D: nodal layout only
   int rc = (op & 0xff) == OP_DEC_QUANT  ? check_quant_args(p, in, out, ws, x.tau)
            : (op & 0xff) == OP_REC_DEQ ? check_quant_args(p, out, in, ws, x.tau)
                                         : check_op_args(p, in, out, ws, !packed_op(op));
@@ -283,7 +285,9 @@ int mgr_plan_create(mgr_ctx* ctx, const mgr_desc* desc, mgr_plan** plan) {
     p->ws_b = L >= 2 ? align_up(size_t(p->geom[L - 1].coarse_count()) * p->welem) : 0;
     p->ws_f = align_up(size_t(p->geom[L].coarse_count()) * p->welem);
   }
-  p->ws_bytes = p->ws_a + p->ws_b + p->ws_f;
+  if (L >= 1 && desc->ndim == 4)
+    p->ws_g = align_up(size_t(p->geom[L].tax.n) * size_t(p->geom[L].space_coarse()) * p->welem);
+  p->ws_bytes = p->ws_a + p->ws_b + p->ws_f + p->ws_g;
   ctx->live_plans.fetch_add(1);
   *plan = p;
   return MGR_OK;
@@ -335,7 +339,7 @@ int mgr_recompose_packed(const mgr_plan* p, const void* in, int nclasses, void* 
 }
 
 int mgr_quant_bins(const mgr_plan* p, double tau, double* bins, int cap) {
-  if (!p || (cap > 0 && !bins)) return MGR_EINVAL;
+  if (!p || (cap > 0 && !bins) || p->desc.ndim == 4) return MGR_EINVAL;
   std::vector<double> b;
   int rc;
   try {
@@ -377,6 +381,7 @@ int mgr_recompose_host(const mgr_plan* p, const void* host_in, void* host_out, v
 int mgr_profile(const mgr_plan* p, int op, const void* in, void* out, void* ws, mgr_stream_t stream,
                 mgr_kernel_time* times, int cap, int* n) {
   if (!n || (cap > 0 && !times) || op < OP_DEC || op > OP_REC_PACKED || !p) return MGR_EINVAL;
+  if (p->desc.ndim == 4 && packed_op(op)) return MGR_EINVAL;
   if (op == OP_REC_PACKED) op |= (p->levels + 1) << 8;
   int rc = check_op_args(p, in, out, ws, !packed_op(op));
   if (rc != MGR_OK) return rc;

@@ -832,6 +832,7 @@ int batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket)
     const mgr_request& r = reqs[i];
     if (!r.plan || !r.in || !r.out || r.in == r.out) return MGR_EINVAL;
     if (r.plan->ctx != ctx) return MGR_EINVAL;
+    if (r.plan->desc.ndim == 4) return MGR_EINVAL;  // the batched kernels are 1D-3D
     if (form < 0) form = r.plan->form;
     if (r.plan->form != form) return MGR_EINVAL;
     if (r.op == 0) dec.push_back(&r);

@@ -118,7 +118,7 @@ bool overlap(const void* a, const void* b, size_t n) {
 }
 
 int check(const mgr_plan* p, const void* a, const void* b) {
-  if (!p || !a || !b) return MGR_EINVAL;
+  if (!p || !a || !b || p->desc.ndim == 4) return MGR_EINVAL;
   if ((reinterpret_cast<uintptr_t>(a) % p->elem) || (reinterpret_cast<uintptr_t>(b) % p->elem)) return MGR_EINVAL;
   if (overlap(a, b, size_t(p->count) * p->elem)) return MGR_EINVAL;
   if (cudaPeekAtLastError() != cudaSuccess) {
@@ -143,7 +143,7 @@ cudaError_t enqueue_unpack_classes(const mgr_plan* p, const void* packed, int nc
 extern "C" {
 
 int mgr_class_offsets(const mgr_plan* p, int64_t* offsets, int cap, int* nclasses) {
-  if (!p || !nclasses || (cap > 0 && !offsets)) return MGR_EINVAL;
+  if (!p || !nclasses || (cap > 0 && !offsets) || p->desc.ndim == 4) return MGR_EINVAL;
   const int n = p->levels + 2;
   for (int i = 0; i < std::min(cap, n); ++i) offsets[i] = p->class_off[i];
   *nclasses = p->levels + 1;

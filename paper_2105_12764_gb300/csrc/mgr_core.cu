@@ -40,28 +40,10 @@ thread_local Recorder* t_recorder = nullptr;
 
 namespace {
 
-// Optional per-launch CUDA-event instrumentation (mgr_profile).
-inline void rec_begin(cudaStream_t st) {
-  if (!t_recorder) return;
-  LaunchRecord r{};
-  cudaEventCreate(&r.start);
-  cudaEventCreate(&r.stop);
-  cudaEventRecord(r.start, st);
-  t_recorder->launches.push_back(r);
-}
-inline void rec_end(cudaStream_t st, const char* name, int level, double bytes, double flops) {
-  if (!t_recorder) return;
-  LaunchRecord& r = t_recorder->launches.back();
-  cudaEventRecord(r.stop, st);
-  std::snprintf(r.name, sizeof(r.name), "%s", name);
-  r.level = level;
-  r.bytes = bytes;
-  r.flops = flops;
-}
-
 #include "mgr_device.cuh"
 #include "mgr_level.cuh"
 #include "mgr_solve.cuh"
+#include "mgr_launch.cuh"
 
 // ---------------------------------------------------------------------------
 // In-place decomposition of the finest level: coefficients written pointwise
@@ -97,223 +79,6 @@ __global__ void k_coef_inplace(TD* y, int nz, int ny, int nx, const TS* waz, con
   }
 }
 
-// ---------------------------------------------------------------------------
-// Host-side level loops
-// ---------------------------------------------------------------------------
-
-template <typename T>
-const T* table(const mgr_plan* p);
-template <>
-const double* table<double>(const mgr_plan* p) { return p->tables.d64; }
-template <>
-const float* table<float>(const mgr_plan* p) { return p->tables.d32; }
-
-inline int grid_1d(int64_t total, int block, const mgr_plan* p) {
-  int64_t g = (total + block - 1) / block;
-  int64_t cap = int64_t(p->ctx->num_sms) * 32;
-  return int(std::max<int64_t>(1, std::min(g, cap)));
-}
-
-struct Bufs {
-  void* A;
-  void* B;
-  void* F;
-};
-
-inline Bufs split_ws(const mgr_plan* p, void* ws) {
-  char* b = static_cast<char*>(ws);
-  return Bufs{b, b + p->ws_a, b + p->ws_a + p->ws_b};
-}
-
-constexpr int kInterpNW = 8, kInterpRPW = 2;
-
-template <typename TS, typename TW>
-LevelArgs<TS, TW> level_args(const mgr_plan* p, int l) {
-  const LevelGeom& g = p->geom[l];
-  LevelArgs<TS, TW> a{};
-  const TS* T = table<TS>(p);
-  for (int k = 0; k < 3; ++k) {
-    a.n[k] = g.ax[k].n;
-    a.m[k] = g.ax[k].m;
-    a.s[k] = g.ax[k].s;
-    a.N[k] = g.ax[k].N;
-    a.wa[k] = T + g.ax[k].o_wa;
-    a.wb[k] = T + g.ax[k].o_wb;
-    a.k[k] = T + g.ax[k].o_k;
-  }
-  a.y_sz = p->full[1] * p->full[2];
-  a.y_sy = p->full[2];
-  a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
-  a.c_sy = g.ax[2].m;
-  return a;
-}
-
-// Number of z chunks for `tiles` xy tiles and mz coarse planes: minimise
-// waves x planes streamed per CTA (each chunk also streams ~1.5 halo planes).
-inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_sm) {
-  const int64_t slots = int64_t(p->ctx->num_sms) * ctas_per_sm;
-  int best = 1;
-  double best_cost = 1e300;
-  const int cmax = std::max(1, std::min(mz, 64));
-  for (int c = 1; c <= cmax; ++c) {
-    const int len = (mz + c - 1) / c;
-    if (c > 1 && len < 4) break;
-    const int cc = (mz + len - 1) / len;
-    const int64_t waves = (tiles * cc + slots - 1) / slots;
-    const double cost = double(waves) * (len + 1.5);
-    if (cost < best_cost - 1e-9) {
-      best_cost = cost;
-      best = c;
-    }
-  }
-  return best;
-}
-
-template <typename TS, typename TW>
-dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
-  using C = LevelCfg<TS>;
-  using G = LevelTile<C::NW, C::RPW>;
-  const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
-  a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
-  const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
-  return dim3(gx, gy, gz);
-}
-
-template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ = false>
-void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
-  using C = LevelCfg<TS>;
-  constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
-  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  dim3 grid = level_grid(p, a);
-  kern<<<grid, C::NW * 32, sm, st>>>(a);
-}
-
-// c: nodal coefficients (PK false), the packed class of level l (PK true), or
-// null for a dropped class (all coefficients zero); QZ: c holds codes of bin
-// width qs
-template <typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ = false>
-void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st,
-                   double qs = 1.0) {
-  const LevelGeom& g = p->geom[l];
-  const TS* T = table<TS>(p);
-  InterpArgs<TS, TW> a{};
-  for (int k = 0; k < 3; ++k) {
-    a.n[k] = g.ax[k].n;
-    a.m[k] = g.ax[k].m;
-    a.s[k] = g.ax[k].s;
-    a.N[k] = g.ax[k].N;
-    a.wa[k] = T + g.ax[k].o_wa;
-    a.wb[k] = T + g.ax[k].o_wb;
-  }
-  a.c = c;
-  a.y_sz = PK ? int64_t(g.ax[1].n) * g.ax[2].n : p->full[1] * p->full[2];
-  a.y_sy = PK ? int64_t(g.ax[2].n) : p->full[2];
-  a.w = w;
-  a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
-  a.c_sy = g.ax[2].m;
-  a.out = out;
-  a.out_full = out_full;
-  a.qs = qs;
-  a.o_sz = out_full ? a.y_sz : int64_t(g.ax[1].n) * g.ax[2].n;
-  a.o_sy = out_full ? a.y_sy : int64_t(g.ax[2].n);
-  constexpr int BY = kInterpNW * kInterpRPW;
-  const int gx = (a.m[2] + 31) / 32, gy = (a.m[1] + BY - 1) / BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
-  a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
-  const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
-  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
-  auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK, QZ>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
-}
-
-template <typename TW>
-cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st);
-
-template <typename TW>
-cudaError_t solve_axis(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st) {
-  const Work wk = work_solve(p, l, axis, op != SOLVE_INPLACE);
-  static const char* names[3] = {"solve_z", "solve_y", "solve_x"};
-  rec_begin(st);
-  cudaError_t err = solve_axis_launch<TW>(p, l, axis, f, w, op, st);
-  rec_end(st, names[axis], l, wk.bytes, wk.flops);
-  return err;
-}
-
-template <typename TW>
-cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st) {
-  const LevelGeom& g = p->geom[l];
-  const int mz = g.ax[0].m, my = g.ax[1].m, mx = g.ax[2].m;
-  const TW* T = table<TW>(p);
-  const TW* ta = T + g.ax[axis].o_ta;
-  const TW* tb = T + g.ax[axis].o_tb;
-  const int64_t lines_x = int64_t(mz) * my;
-  if (axis == 2 && sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
-    // lines too long to stage in shared memory: one thread per line from global memory
-    const int threads = 128;
-    const int blocks = int((lines_x + threads - 1) / threads);
-    k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, lines_x, mx, ta, tb, op);
-    return cudaGetLastError();
-  }
-  if (axis == 2) {
-    const int pitch = mx | 1;
-    // rows per CTA (one solving thread per row, 128 threads load and store):
-    // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
-    int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
-    R = std::max(1, R);
-    const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
-    const int blocks = int((lines_x + R - 1) / R);
-    cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines_x, mx, R, ta, tb, op);
-    return cudaGetLastError();
-  }
-  int mline, inner;
-  int64_t lstride, outer, ostride;
-  if (axis == 1) {
-    mline = my; lstride = mx; inner = mx; outer = mz; ostride = int64_t(my) * mx;
-  } else {
-    mline = mz; lstride = int64_t(my) * mx; inner = mx; outer = my; ostride = mx;
-  }
-  const int64_t lines = int64_t(inner) * outer;
-  const int threads = 128;
-  const int blocks = int((lines + threads - 1) / threads);
-  k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb, op);
-  return cudaGetLastError();
-}
-
-// solve along every active axis, x first; the last one applies `final_op` into w
-template <typename TW>
-cudaError_t solve_level(const mgr_plan* p, int l, TW* f, TW* w, int final_op, cudaStream_t st) {
-  const LevelGeom& g = p->geom[l];
-  int last = -1;
-  for (int axis = 2; axis >= 0; --axis)
-    if (g.ax[axis].active) last = axis;
-  for (int axis = 2; axis >= 0; --axis) {
-    if (!g.ax[axis].active) continue;
-    cudaError_t e = solve_axis<TW>(p, l, axis, f, w, axis == last ? final_op : SOLVE_INPLACE, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-// Coarsest grid <-> its place in the output: the nodal positions at stride
-// 2^L (nodal layout) or class 0, the compact coarsest grid (packed layout).
-template <typename TD, typename TW>
-cudaError_t coarsest_copy_launch(const mgr_plan* p, TD* y, TW* w, bool packed, int dir, cudaStream_t st) {
-  const int L = p->levels;
-  const int3 n0 = make_int3(int(p->coarsest[0]), int(p->coarsest[1]), int(p->coarsest[2]));
-  const int64_t s0 = packed ? 1 : (int64_t(1) << L);
-  const longlong3 s = make_longlong3(p->full[0] > 1 ? s0 : 1, p->full[1] > 1 ? s0 : 1, s0);
-  const longlong3 N = packed ? make_longlong3(n0.x, n0.y, n0.z) : make_longlong3(p->full[0], p->full[1], p->full[2]);
-  const int64_t total = int64_t(n0.x) * n0.y * n0.z;
-  rec_begin(st);
-  k_coarsest<TD, TW><<<grid_1d(total, 256, p), 256, 0, st>>>(y, N.y * N.z, N.z, w, n0, s, N, dir);
-  cudaError_t e = cudaGetLastError();
-  rec_end(st, "coarsest", 0, double(total) * (sizeof(TD) + sizeof(TW)), 0.0);
-  return e;
-}
 
 // Class 0 of a quantized decomposition: codes of the compact coarsest values
 // v (dir 1) or those values from their codes (dir 0), arithmetic and rounding
@@ -526,6 +291,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
 }  // namespace
 
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+  if (p->desc.ndim == 4) return enqueue_decompose_st(p, in, out, ws, st);
   switch (p->form) {
     case kFormF64: return decompose_t<double, double, double, false>(p, in, out, ws, st);
     case kFormF32: return decompose_t<float, float, float, false>(p, in, out, ws, st);
@@ -534,6 +300,7 @@ cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void
 }
 
 cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
+  if (p->desc.ndim == 4) return enqueue_recompose_st(p, in, out, ws, st);
   const int all = p->levels + 1;
   switch (p->form) {
     case kFormF64: return recompose_t<double, double, double, false>(p, in, out, ws, st, all);

@@ -2,7 +2,9 @@
 //
 // Axes are always handled as three: axis 0 (slowest) .. axis 2 (fastest).  A
 // field with ndim < 3 is embedded with leading axes of length 1 that never
-// coarsen ("inactive").
+// coarsen ("inactive").  A 4D (spatiotemporal) field has one more axis, time,
+// slower than the three spatial ones; it is kept apart (LevelGeom::tax) so the
+// spatial kernels see every time slice as a 3D field.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,8 +46,11 @@ struct AxisLevel {
 
 struct LevelGeom {
   AxisLevel ax[kAxes];
-  int64_t fine_count() const { return (int64_t)ax[0].n * ax[1].n * ax[2].n; }
-  int64_t coarse_count() const { return (int64_t)ax[0].m * ax[1].m * ax[2].m; }
+  AxisLevel tax;  // time axis of a 4D field (inactive, n = m = 1, otherwise)
+  int64_t space_fine() const { return (int64_t)ax[0].n * ax[1].n * ax[2].n; }
+  int64_t space_coarse() const { return (int64_t)ax[0].m * ax[1].m * ax[2].m; }
+  int64_t fine_count() const { return space_fine() * tax.n; }
+  int64_t coarse_count() const { return space_coarse() * tax.m; }
 };
 
 // Host-side FP64 tables of a plan (built from the coordinates) and their
@@ -73,11 +78,13 @@ struct mgr_plan {
   int form = 0;
   int levels = 0;                     // L
   int64_t full[mgr::kAxes] = {1, 1, 1};
+  int64_t full_t = 1;                 // time axis length (4D fields), else 1
   int64_t count = 0;                  // prod(shape)
   size_t elem = 0;                    // bytes per field element
   size_t welem = 0;                   // bytes per workspace element
   std::vector<mgr::LevelGeom> geom;   // geom[l] for l = 1..L (geom[0] unused)
   int64_t coarsest[mgr::kAxes] = {1, 1, 1};
+  int64_t coarsest_t = 1;
   // class-packed layout: class c (0 = coarsest grid, l = coefficients of level
   // l) starts at class_off[c]; class_off[L+1] = count
   std::vector<int64_t> class_off;
@@ -87,7 +94,7 @@ struct mgr_plan {
   std::vector<double> znorm;
   mgr::Tables tables;
   // workspace layout (bytes)
-  size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_bytes = 0;
+  size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_g = 0, ws_bytes = 0;  // ws_g: 4D time-slice load vectors
   // launch-sequence cache: one CUDA graph per (op, in, out, workspace)
   std::mutex graph_mu;
   struct GraphEntry {
@@ -138,6 +145,9 @@ void batch_destroy(mgr_ctx* ctx);
 // mgr_core.cu: enqueue one whole operation (all levels) on `st` (no graph).
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+// mgr_st.cu: the 4D (spatiotemporal) form of the two operations
+cudaError_t enqueue_decompose_st(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+cudaError_t enqueue_recompose_st(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 // class-packed output / input (recompose from classes 0..ncls-1)
 cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,

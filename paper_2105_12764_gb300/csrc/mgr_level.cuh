@@ -163,6 +163,8 @@ struct LevelArgs {
   int write_y;
   double qs;                // QZ: 1/bin width (MODE 0) or bin width (MODE 1)
   unsigned long long* qsat; // QZ, MODE 0: saturated-code counter (may be null)
+  int all_fine;             // MODE 1: every node holds a coefficient (a time slice of a
+                            // 4D field that is fine in time), not only the fine ones
 };
 
 // FP64 keeps the x / y stencil weights in shared memory (the FP64 pass is
@@ -489,6 +491,11 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         c[1] = vc[k][1] - In[k][1];
         c[2] = vc[k][2] - In[k][2];
         c[3] = vc[k][3] - In[k][3];
+      } else if (a.all_fine) {
+        c[0] = (vx0 && vy0[k]) ? vc[k][0] : TS(0);
+        c[1] = (vx1 && vy0[k]) ? vc[k][1] : TS(0);
+        c[2] = (vx0 && vy1[k]) ? vc[k][2] : TS(0);
+        c[3] = (vx1 && vy1[k]) ? vc[k][3] : TS(0);
       } else {
         c[0] = TS(0);
         c[1] = fx1 ? vc[k][1] : TS(0);
@@ -567,7 +574,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         for (int h = 0; h < 2; ++h) {
           const int r = 2 * (warp * RPW + k) + h;
           // rows coarse in y (of the coarse-z plane): c vanishes on coarse columns
-          const bool zero_row = h == 0 || !fy1[k];
+          const bool zero_row = (h == 0 || !fy1[k]) && !(MODE == 1 && a.all_fine);
           TS g, gf = TS(0);
           if (kx_generic) {
             const TS* row = cc + r * CP + dx - 2;

@@ -38,7 +38,7 @@ int levels_until(int64_t n, int64_t stop) {
 }  // namespace
 
 int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels) {
-  if (!d || d->ndim < 1 || d->ndim > 3) return MGR_EINVAL;
+  if (!d || d->ndim < 1 || d->ndim > 4) return MGR_EINVAL;
   int mx = 1 << 30, df = 1 << 30;
   for (int k = 0; k < d->ndim; ++k) {
     if (d->shape[k] < 2 || d->shape[k] > (int64_t(1) << 30)) return MGR_EINVAL;
@@ -58,36 +58,51 @@ int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default
 int build_plan_tables(mgr_plan* p) {
   const mgr_desc& d = p->desc;
   const int L = p->levels;
-  // full-grid coordinates per internal axis (axis kAxes-1 = fastest)
-  std::vector<double> xs[kAxes];
-  const int lead = kAxes - d.ndim;
+  // full-grid coordinates per internal axis (axis kAxes-1 = fastest); entry
+  // kAxes is the time axis of a 4D field (desc axis 0)
+  const bool st = d.ndim == 4;
+  const int nsp = st ? 3 : d.ndim;  // spatial dimensions
+  const int lead = kAxes - nsp;
+  std::vector<double> xs[kAxes + 1];
+  auto load_axis = [&](int k, std::vector<double>& x) {
+    const int64_t N = d.shape[k];
+    x.resize(N);
+    for (int64_t i = 0; i < N; ++i) x[i] = d.coords[k] ? d.coords[k][i] : double(i);
+    for (int64_t i = 1; i < N; ++i)
+      if (!(x[i] > x[i - 1]) || !std::isfinite(x[i])) return false;
+    return std::isfinite(x[0]);
+  };
   for (int a = 0; a < kAxes; ++a) {
     if (a < lead) {
       p->full[a] = 1;
       xs[a].assign(1, 0.0);
       continue;
     }
-    const int k = a - lead;
-    const int64_t N = d.shape[k];
-    p->full[a] = N;
-    xs[a].resize(N);
-    for (int64_t i = 0; i < N; ++i) xs[a][i] = d.coords[k] ? d.coords[k][i] : double(i);
-    for (int64_t i = 1; i < N; ++i)
-      if (!(xs[a][i] > xs[a][i - 1]) || !std::isfinite(xs[a][i])) return MGR_EINVAL;
-    if (!std::isfinite(xs[a][0])) return MGR_EINVAL;
+    const int k = a - lead + (st ? 1 : 0);
+    p->full[a] = d.shape[k];
+    if (!load_axis(k, xs[a])) return MGR_EINVAL;
+  }
+  p->full_t = st ? d.shape[0] : 1;
+  if (st) {
+    if (!load_axis(0, xs[kAxes])) return MGR_EINVAL;
+  } else {
+    xs[kAxes].assign(1, 0.0);
   }
   std::vector<double>& T = p->tables.host;
   T.clear();
   p->geom.assign(L + 1, LevelGeom{});
+  auto axref = [&](int l, int a) -> AxisLevel& { return a < kAxes ? p->geom[l].ax[a] : p->geom[l].tax; };
   // level sizes per axis: n_L = N, n_{l-1} = n_l/2 + 1
-  for (int a = 0; a < kAxes; ++a) {
-    int64_t n = p->full[a];
+  for (int a = 0; a <= kAxes; ++a) {
+    const int64_t full = a < kAxes ? p->full[a] : p->full_t;
+    const bool inactive = a < kAxes ? a < lead : !st;
+    int64_t n = full;
     for (int l = L; l >= 1; --l) {
-      AxisLevel& ax = p->geom[l].ax[a];
-      ax.N = p->full[a];
+      AxisLevel& ax = axref(l, a);
+      ax.N = full;
       ax.s = int64_t(1) << (L - l);
       ax.n = int(n);
-      if (a < lead) {
+      if (inactive) {
         ax.m = 1;
         ax.active = false;
       } else {
@@ -96,11 +111,12 @@ int build_plan_tables(mgr_plan* p) {
         n = ax.m;
       }
     }
-    p->coarsest[a] = n;
+    if (a < kAxes) p->coarsest[a] = n;
+    else p->coarsest_t = n;
   }
   // class sizes: the coarsest grid, then |N_l| - |N_{l-1}| per level
   p->class_off.assign(L + 2, 0);
-  p->class_off[1] = p->coarsest[0] * p->coarsest[1] * p->coarsest[2];
+  p->class_off[1] = p->coarsest[0] * p->coarsest[1] * p->coarsest[2] * p->coarsest_t;
   for (int l = 1; l <= L; ++l)
     p->class_off[l + 1] = p->class_off[l] + p->geom[l].fine_count() - p->geom[l].coarse_count();
   auto push = [&](size_t count) {
@@ -111,8 +127,8 @@ int build_plan_tables(mgr_plan* p) {
     return off;
   };
   for (int l = L; l >= 1; --l) {
-    for (int a = 0; a < kAxes; ++a) {
-      AxisLevel& ax = p->geom[l].ax[a];
+    for (int a = 0; a <= kAxes; ++a) {
+      AxisLevel& ax = axref(l, a);
       const int n = ax.n, m = ax.m;
       ax.o_wa = push(n);
       ax.o_wb = push(n);

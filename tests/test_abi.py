@@ -59,7 +59,7 @@ def test_host_only_entry_points(lib_path):
 
     assert mgr.lib.mgr_version().decode().count(".") == 2
     assert mgr.mgr_strerror(mgr.MGR_EINVAL) == "invalid argument"
-    for shape in [(2,), (5,), (65,), (513,), (1000, 700, 300), (17, 17), (24, 9, 33), (3, 100)]:
+    for shape in [(2,), (5,), (65,), (513,), (1000, 700, 300), (17, 17), (24, 9, 33), (3, 100), (9, 17, 33, 65)]:
         assert mgr.max_levels(shape) == oracle.max_levels(shape)
         assert mgr.default_levels(shape) == oracle.default_levels(shape)
     with pytest.raises(mgr.MgrError):
