@@ -60,9 +60,14 @@ typedef enum {
 } mgr_precision;
 
 /* Problem description (Sec. II.A: a d-dimensional field on a rectilinear
-   grid; Sec. IV.A: FP32 or FP64 nodal values). */
+   grid; Sec. IV.A: FP32 or FP64 nodal values).  ndim = 4 is the
+   spatiotemporal (3+1)-D form of Sec. III.E: shape[0] is time, decomposed
+   with the other three axes as one more tensor-product dimension.  4D plans
+   run mgr_decompose / mgr_recompose (and their _host and _noalloc forms and
+   the serving layer) out of place (in == out is MGR_EINVAL) in the nodal
+   layout; the class-packed, quantized and batched forms are 1D-3D only. */
 typedef struct {
-  int ndim;                /* 1..3                                                   */
+  int ndim;                /* 1..4                                                   */
   int64_t shape[4];        /* shape[0..ndim-1], each >= 2; shape[ndim-1] fastest     */
   const double* coords[4]; /* HOST, strictly increasing, length shape[k]; NULL means
                               uniform unit spacing x_i = i.  Copied at plan time;
