@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--shape", default=None, help="override, e.g. 257,257,257")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-classes", action="store_true")
+    ap.add_argument("--no-st", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
@@ -364,6 +365,9 @@ def run_ours(args):
     # ---- class-packed layout and progressive recomposition (same FP64 field)
     if not args.no_classes:
         result["classes"] = classes_section(mgr, ctx, u, max(3, min(args.steps, 20)), args.warmup, t_dec + t_rec)
+    # ---- spatiotemporal (3+1)-D form
+    if not args.no_st:
+        result["spatiotemporal"] = st_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup)
     # ---- batched form (4096 uneven fields) and served form (Poisson request stream)
     if not args.no_batch:
         result["batched"] = batched_section(mgr, ctx, max(2, min(args.steps, 10)))
@@ -438,6 +442,57 @@ def classes_section(mgr, ctx, u_np, steps, warmup, nodal_ms):
                        "tolerance tau = rel x (max - min) of the field"}
     plan.close()
     del x, pk, z, wsb, codes, sat
+    torch.cuda.empty_cache()
+    return out
+
+
+ST_SHAPE = (33, 129, 129, 129)
+
+
+def st_section(mgr, ctx, steps, warmup):
+    """4D field (33 time steps of 129^3, FP64, k^-5/3 space-time random field):
+    decompose + recompose per step, same metric as the headline."""
+    import torch
+
+    from paper_2105_12764_gb300 import synth
+
+    shape = ST_SHAPE
+    x = synth.grf_field_torch(shape, seed=5)
+    plan = mgr.Plan(ctx, shape, None, -1, mgr.MGR_F64)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    wsb = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.decompose(x, y, wsb, st)
+        plan.recompose(y, z, wsb, st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    for _ in range(steps):
+        plan.decompose(x, y, wsb, st)
+    ev[1].record(st)
+    for _ in range(steps):
+        plan.recompose(y, z, wsb, st)
+    ev[2].record(st)
+    torch.cuda.synchronize()
+    t_dec = ev[0].elapsed_time(ev[1]) / steps
+    t_rec = ev[1].elapsed_time(ev[2]) / steps
+    rt = float((z - x).abs().max().item() / x.abs().max().item())
+    agg = {}
+    for op, (src, dst) in ((0, (x, y)), (1, (y, z))):
+        for r in plan.profile(op, src, dst, wsb):
+            a = agg.setdefault(r["name"], 0.0)
+            agg[r["name"]] = a + r["ms"]
+    tot = sum(agg.values())
+    nb = x.numel() * 8
+    out = {"value": round(2.0 * nb / ((t_dec + t_rec) * 1e-3) / 1e9, 3), "unit": UNIT,
+           "decompose_gbs": round(nb / (t_dec * 1e-3) / 1e9, 3), "recompose_gbs": round(nb / (t_rec * 1e-3) / 1e9, 3),
+           "ms_per_step": round(t_dec + t_rec, 4), "round_trip_rel_err": rt, "levels": plan.levels,
+           "kernel_share": {k: round(v / tot, 4) for k, v in sorted(agg.items(), key=lambda kv: -kv[1])},
+           "workload": f"{'x'.join(map(str, shape))} (t, z, y, x) FP64 space-time k^-5/3 random field, full 4D "
+                       "hierarchy, decompose + recompose per step"}
+    plan.close()
+    del x, y, z, wsb
     torch.cuda.empty_cache()
     return out
 

@@ -172,6 +172,39 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
   kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
 }
 
+// Thomas solves along the contiguous axis: `lines` lines of length mx,
+// consecutive in memory.
+template <typename TW>
+cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t lines, const TW* ta, const TW* tb, int op,
+                           cudaStream_t st) {
+  (void)p;
+  if (sizeof(TW) == 8 && lines >= 32768) {
+    // FP64 with many lines: the recurrences' FP64 latency needs more lines in
+    // flight per SM than whole lines staged in shared memory allow
+    const int64_t nwarps = (lines + 31) / 32;
+    k_solve_rows<TW><<<int((nwarps + kRowsWarps - 1) / kRowsWarps), kRowsWarps * 32, 0, st>>>(f, w, mx, lines, mx, ta,
+                                                                                             tb, op);
+    return cudaGetLastError();
+  }
+  if (sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
+    // lines too long to stage in shared memory: one thread per line from global memory
+    const int threads = 128;
+    const int blocks = int((lines + threads - 1) / threads);
+    k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, lines, mx, ta, tb, op);
+    return cudaGetLastError();
+  }
+  const int pitch = mx | 1;
+  // rows per CTA (one solving thread per row, 128 threads load and store):
+  // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
+  int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
+  R = std::max(1, R);
+  const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
+  const int blocks = int((lines + R - 1) / R);
+  cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines, mx, R, ta, tb, op);
+  return cudaGetLastError();
+}
+
 template <typename TW>
 cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st);
 
@@ -193,25 +226,7 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   const TW* ta = T + g.ax[axis].o_ta;
   const TW* tb = T + g.ax[axis].o_tb;
   const int64_t lines_x = int64_t(mz) * my;
-  if (axis == 2 && sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
-    // lines too long to stage in shared memory: one thread per line from global memory
-    const int threads = 128;
-    const int blocks = int((lines_x + threads - 1) / threads);
-    k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, lines_x, mx, ta, tb, op);
-    return cudaGetLastError();
-  }
-  if (axis == 2) {
-    const int pitch = mx | 1;
-    // rows per CTA (one solving thread per row, 128 threads load and store):
-    // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
-    int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
-    R = std::max(1, R);
-    const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
-    const int blocks = int((lines_x + R - 1) / R);
-    cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines_x, mx, R, ta, tb, op);
-    return cudaGetLastError();
-  }
+  if (axis == 2) return launch_x_solve<TW>(p, f, w, mx, lines_x, ta, tb, op, st);
   int mline, inner;
   int64_t lstride, outer, ostride;
   if (axis == 1) {

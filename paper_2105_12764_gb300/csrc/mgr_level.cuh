@@ -216,8 +216,9 @@ __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bo
 // `in` as the class of this level; y_sz / in_sz = n1*n2, y_sy / in_sy = n2).
 // QZ (with PK): those coefficients are int32 codes (TD = int in MODE 0, TI =
 // int in MODE 1).
+// AF: honour `all_fine` (the 4D form's time slices; a runtime flag read once).
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK = false,
-          bool QZ = false>
+          bool QZ = false, bool AF = false>
 __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, int by, int bz,
                                            unsigned char* smem_raw) {
   using G = LevelTile<NW, RPW>;
@@ -249,6 +250,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const TI* __restrict__ in = static_cast<const TI*>(a.in);
   TD* __restrict__ yout = static_cast<TD*>(a.y);
   const bool wy = (MODE == 0) && a.write_y;
+  const bool afine = AF && MODE == 1 && a.all_fine;
   const TS qs = QZ ? TS(a.qs) : TS(1);
   // value written for coefficient v when `st` (the node is stored: values of
   // nodes that are not stored are never quantized, so never counted as
@@ -491,7 +493,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         c[1] = vc[k][1] - In[k][1];
         c[2] = vc[k][2] - In[k][2];
         c[3] = vc[k][3] - In[k][3];
-      } else if (a.all_fine) {
+      } else if (afine) {
         c[0] = (vx0 && vy0[k]) ? vc[k][0] : TS(0);
         c[1] = (vx1 && vy0[k]) ? vc[k][1] : TS(0);
         c[2] = (vx0 && vy1[k]) ? vc[k][2] : TS(0);
@@ -574,7 +576,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         for (int h = 0; h < 2; ++h) {
           const int r = 2 * (warp * RPW + k) + h;
           // rows coarse in y (of the coarse-z plane): c vanishes on coarse columns
-          const bool zero_row = (h == 0 || !fy1[k]) && !(MODE == 1 && a.all_fine);
+          const bool zero_row = (h == 0 || !fy1[k]) && !afine;
           TS g, gf = TS(0);
           if (kx_generic) {
             const TS* row = cc + r * CP + dx - 2;

@@ -154,6 +154,77 @@ __global__ void __launch_bounds__(128) k_solve_contig(TW* __restrict__ f, TW* __
   solve_contig_rows<TW>(f, w, mline, rows, row_pitch, R, ta, tb, op, blockIdx.x * int64_t(R), smem_raw);
 }
 
+// Lines along the contiguous axis, 32 per warp (lane = line): the warp moves
+// its lines through a 32 x 32 shared-memory tile (row segments loaded and
+// stored coalesced, transposed in the tile), each lane runs its line's
+// recurrence through the tile's columns.  The forward sweep writes y back to
+// f, the backward sweep reads it again; no whole line is held on chip, so
+// many warps (hence many independent recurrences) fit on an SM.
+constexpr int kRowsWarps = 4;
+
+template <typename TW>
+__global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__ f, TW* __restrict__ w, int mline,
+                                                                int64_t rows, int64_t row_pitch,
+                                                                const TW* __restrict__ ta, const TW* __restrict__ tb,
+                                                                int op) {
+  __shared__ TW tiles[kRowsWarps][32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t(blockIdx.x) * kRowsWarps + warp) * 32;
+  if (r0 >= rows) return;
+  const int nr = int(rows - r0 < 32 ? rows - r0 : 32);
+  TW(*tile)[33] = tiles[warp];
+  TW* base = f + r0 * row_pitch;
+  const bool act = lane < nr;
+  TW prev = TW(0);
+  for (int c0 = 0; c0 < mline; c0 += 32) {
+    const int nc = min(32, mline - c0);
+    if (lane < nc) {
+#pragma unroll 8
+      for (int i = 0; i < nr; ++i) tile[lane][i] = base[int64_t(i) * row_pitch + c0 + lane];
+    }
+    __syncwarp();
+    if (act) {
+      for (int c = 0; c < nc; ++c) {
+        prev = tile[c][lane] - ta[c0 + c] * prev;
+        tile[c][lane] = prev;
+      }
+    }
+    __syncwarp();
+    if (lane < nc) {
+#pragma unroll 8
+      for (int i = 0; i < nr; ++i) base[int64_t(i) * row_pitch + c0 + lane] = tile[lane][i];
+    }
+    __syncwarp();
+  }
+  TW* wb = w + r0 * row_pitch;
+  TW next = TW(0);
+  for (int c0 = ((mline - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
+    const int nc = min(32, mline - c0);
+    if (lane < nc) {
+#pragma unroll 8
+      for (int i = 0; i < nr; ++i) tile[lane][i] = base[int64_t(i) * row_pitch + c0 + lane];
+    }
+    __syncwarp();
+    if (act) {
+      for (int c = nc - 1; c >= 0; --c) {
+        next = tile[c][lane] - tb[c0 + c] * next;
+        tile[c][lane] = next;
+      }
+    }
+    __syncwarp();
+    if (lane < nc) {
+#pragma unroll 8
+      for (int i = 0; i < nr; ++i) {
+        const int64_t g = int64_t(i) * row_pitch + c0 + lane;
+        if (op == SOLVE_INPLACE) base[g] = tile[lane][i];
+        else if (op == SOLVE_ADD) wb[g] = wb[g] + tile[lane][i];
+        else wb[g] = wb[g] - tile[lane][i];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Coarsest grid <-> nodal positions (dir 0: gather nodal -> compact; 1: scatter)
 template <typename TD, typename TW>
 __device__ __forceinline__ void coarsest_copy(TD* y, int64_t y_sz, int64_t y_sy, TW* w, int3 n, longlong3 s,

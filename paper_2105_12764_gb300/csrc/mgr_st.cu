@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level_st(const LevelArgs<TS, TW>
   }
   b.f = a.f + int64_t(t) * sl.f_ts;
   b.all_fine = (MODE == 1 && sl.fine_all) ? int(!is_coarse(t, sl.nt)) : 0;
-  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW>(b, blockIdx.x, blockIdx.y, bz, smem_raw);
+  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, false, false, true>(b, blockIdx.x, blockIdx.y, bz, smem_raw);
 }
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
@@ -283,17 +283,7 @@ cudaError_t solve_level_st(const mgr_plan* p, int l, TW* f, TW* w, int final_op,
     const int64_t m = int64_t(mt) * Sm;
     rec_begin(st);
     if (axis == 2) {
-      const int64_t lines = int64_t(mt) * mz * my;
-      if (sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
-        k_solve_strided<TW><<<int((lines + 127) / 128), 128, 0, st>>>(f, w, mx, 1, 1, lines, mx, ta, tb, op);
-      } else {
-        const int pitch = mx | 1;
-        int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
-        R = std::max(1, R);
-        const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
-        cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-        k_solve_contig<TW><<<int((lines + R - 1) / R), 128, sm, st>>>(f, w, mx, lines, mx, R, ta, tb, op);
-      }
+      launch_x_solve<TW>(p, f, w, mx, int64_t(mt) * mz * my, ta, tb, op, st);
     } else {
       int mline, inner;
       int64_t lstride, outer, ostride;
