@@ -194,7 +194,7 @@ def traffic_for(kernel, shape_key, src_hash):
 
 def core_source_hash():
     h = hashlib.sha1()
-    for name in ("mgr_core.cu", "mgr_level.cuh", "mgr_solve.cuh", "mgr_device.cuh"):
+    for name in ("mgr_core.cu", "mgr_level.cuh", "mgr_solve.cuh", "mgr_device.cuh", "mgr_launch.cuh"):
         with open(os.path.join(ROOT, "paper_2105_12764_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
