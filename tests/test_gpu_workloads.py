@@ -80,3 +80,53 @@ def test_c3_mixed_full(ctx):
         assert rel_linf(back, u32) <= 1e-5
     finally:
         r.close()
+
+
+def test_c2_fp64_class_packed_and_progressive_full(ctx, c2_field, c2_oracle):
+    """The class-packed form at the bench size: equal to the oracle's classes; every
+    class recomposes the field; class 0 alone gives the coarsest interpolant."""
+    shape = c2_field.shape
+    plan = mgr.Plan(ctx, shape, None, -1, mgr.MGR_F64)
+    L = plan.levels
+    x = torch.from_numpy(c2_field).cuda()
+    pk = torch.empty(x.numel(), dtype=x.dtype, device="cuda")
+    y = torch.empty_like(x)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    try:
+        plan.decompose_packed(x, pk, ws)
+        torch.cuda.synchronize()
+        want = oracle.pack_classes(c2_oracle, L)
+        assert rel_linf(pk.cpu().numpy(), want) <= 1e-12
+        plan.recompose_packed(pk, L + 1, y, ws)
+        torch.cuda.synchronize()
+        assert rel_linf(y.cpu().numpy(), c2_field) <= 1e-13
+        # prefix of the first L classes (finest class dropped), against the oracle on
+        # its own classes
+        plan.recompose_packed(pk, L, y, ws)
+        torch.cuda.synchronize()
+        prog = oracle.recompose_classes(want, shape, L, None, L)
+        assert rel_linf(y.cpu().numpy(), prog) <= 1e-12
+    finally:
+        plan.close()
+
+
+def test_c2_fp64_quantized_full(ctx, c2_field):
+    """Fused quantization at the bench size: the recomposed field is within tau."""
+    plan = mgr.Plan(ctx, c2_field.shape, None, -1, mgr.MGR_F64)
+    x = torch.from_numpy(c2_field).cuda()
+    codes = torch.empty(x.numel(), dtype=torch.int32, device="cuda")
+    y = torch.empty_like(x)
+    sat = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    try:
+        span = float(c2_field.max() - c2_field.min())
+        for rel in (1e-2, 1e-5):
+            tau = rel * span
+            plan.decompose_quantized(x, codes, tau, ws, sat)
+            plan.recompose_dequantized(codes, plan.levels + 1, tau, y, ws)
+            torch.cuda.synchronize()
+            assert int(sat.item()) == 0
+            err = float((y - x).abs().max().item())
+            assert err <= tau * (1 + 1e-9), (rel, err, tau)
+    finally:
+        plan.close()
