@@ -69,6 +69,25 @@ cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* 
 
 bool packed_op(int op) { return (op & 0xff) >= OP_DEC_PACKED; }
 
+// Enqueue while capturing a graph (graph_mu held): recompositions fork their
+// load-vector passes onto the plan's side stream.
+cudaError_t enqueue_captured(mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t cs, const Extra& x) {
+  const int base = op & 0xff;
+  const bool rec = base == OP_REC || base == OP_REC_PACKED || base == OP_REC_DEQ;
+  if (!rec || p->desc.ndim == 4 || p->levels < 1) return enqueue(p, op, in, out, ws, cs, x);
+  if (!p->side) {
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return cudaErrorMemoryAllocation;
+    p->fork_ev.assign(p->levels + 1, nullptr);
+    for (auto& e : p->fork_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cudaErrorMemoryAllocation;
+  }
+  std::vector<double> bins;
+  if (base == OP_REC_DEQ && mgr::quant_bins(p, x.tau, bins) != MGR_OK) return cudaErrorInvalidValue;
+  const int ncls = base == OP_REC ? p->levels + 1 : (op >> 8);
+  const int kind = base == OP_REC ? 0 : (base == OP_REC_PACKED ? 1 : 2);
+  return mgr::enqueue_recompose_fork(p, kind, in, ncls, bins.data(), out, ws, cs, mgr::ForkCtx{p->side, p->fork_ev.data()});
+}
+
 // Arguments of a quantized operation: the field (elem bytes per element) and
 // the int32 codes must be aligned and must not overlap.
 int check_quant_args(const mgr_plan* p, const void* field, const void* codes, const void* ws, double tau) {
@@ -109,7 +128,7 @@ int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cuda
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue(p, op, in, out, ws, cs, x);
+      cudaError_t e2 = enqueue_captured(p, op, in, out, ws, cs, x);
       e = cudaStreamEndCapture(cs, &graph);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -283,7 +302,15 @@ int mgr_plan_create(mgr_ctx* ctx, const mgr_desc* desc, mgr_plan** plan) {
   if (L >= 1) {
     p->ws_a = align_up(size_t(p->geom[L].coarse_count()) * p->welem);
     p->ws_b = L >= 2 ? align_up(size_t(p->geom[L - 1].coarse_count()) * p->welem) : 0;
-    p->ws_f = align_up(size_t(p->geom[L].coarse_count()) * p->welem);
+    // one load-vector buffer per level, so a recomposition can compute every
+    // level's load vector ahead of its solves
+    p->f_off.assign(L + 1, 0);
+    size_t off = 0;
+    for (int l = L; l >= 1; --l) {
+      p->f_off[l] = off;
+      off += align_up(size_t(p->geom[l].coarse_count()) * p->welem);
+    }
+    p->ws_f = off;
   }
   if (L >= 1 && desc->ndim == 4)
     p->ws_g = align_up(size_t(p->geom[L].tax.n) * size_t(p->geom[L].space_coarse()) * p->welem);
@@ -300,6 +327,8 @@ int mgr_plan_destroy(mgr_plan* p) {
     std::lock_guard<std::mutex> lk(p->graph_mu);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
+    for (cudaEvent_t e : p->fork_ev) cudaEventDestroy(e);
+    if (p->side) cudaStreamDestroy(p->side);
   }
   cudaFree(p->tables.d64);
   cudaFree(p->tables.d32);

@@ -196,9 +196,12 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
 // interpolation only.  PK: `in` is class-packed (its first class_off[ncls]
 // elements are read) and must not overlap `out`.
 // QZ (with PK): `in` holds int32 codes with the bin widths bins[0..L].
+// fk (graph capture only): the load-vector passes of all levels run on
+// fk->side ahead of the solve / interpolation chain on st, each level into its
+// own load-vector buffer; st waits for level l's before its solves.
 template <typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st, int ncls,
-                        const double* bins = nullptr) {
+                        const double* bins = nullptr, const ForkCtx* fk = nullptr) {
   static_assert(PK || !QZ, "quantized input is class-packed");
   using TY = std::conditional_t<QZ, int, TD>;  // coefficient input type
   const int L = p->levels;
@@ -213,7 +216,44 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     }
   }
   Bufs b = split_ws(p, ws);
-  TW* F = static_cast<TW*>(b.F);
+  auto Fl = [&](int l) { return reinterpret_cast<TW*>(static_cast<char*>(b.F) + p->f_off[l]); };
+  // load vector of level l (Sec. II.A.2) from its coefficients, on stream s
+  auto load_vector = [&](int l, cudaStream_t s) -> cudaError_t {
+    const LevelGeom& g = p->geom[l];
+    auto a = level_args<TS, TW>(p, l);
+    a.in = PK ? static_cast<const void*>(static_cast<const TY*>(in) + p->class_off[l]) : in;
+    if (PK) {
+      a.in_full = 0;
+      a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
+      a.in_sy = g.ax[2].n;
+    } else {
+      a.in_full = 1;
+      a.in_sz = a.y_sz;
+      a.in_sy = a.y_sy;
+    }
+    a.f = Fl(l);
+    a.w = nullptr;
+    a.y = nullptr;
+    a.write_y = 0;
+    a.qs = QZ ? bins[l] : 1.0;
+    rec_begin(s);
+    launch_level<1, TY, TY, TS, TW, PK, QZ>(p, a, s);
+    cudaError_t e = cudaGetLastError();
+    const Work wk = work_level_load(p, l, false);
+    rec_end(s, "level_load_rec", l, wk.bytes, wk.flops);
+    return e;
+  };
+  const int last_lv = std::min(L, ncls - 1);  // levels 1..last_lv have their coefficient class
+  const bool fork = fk != nullptr && last_lv >= 1 && t_recorder == nullptr;
+  if (fork) {
+    if (cudaEventRecord(fk->ev[0], st) != cudaSuccess || cudaStreamWaitEvent(fk->side, fk->ev[0], 0) != cudaSuccess)
+      return cudaGetLastError();
+    for (int l = 1; l <= last_lv; ++l) {
+      cudaError_t e = load_vector(l, fk->side);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(fk->ev[l], fk->side)) != cudaSuccess) return e;
+    }
+  }
   // coarsest grid from the nodal positions / class 0
   TW* cur = static_cast<TW*>((L % 2 == 1) ? b.A : b.B);  // level 0 lives where decompose left it
   {
@@ -245,31 +285,9 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
       if (e != cudaSuccess) return e;
       continue;
     }
-    auto a = level_args<TS, TW>(p, l);
-    a.in = cl;
-    if (PK) {
-      a.in_full = 0;
-      a.in_sz = int64_t(g.ax[1].n) * g.ax[2].n;
-      a.in_sy = g.ax[2].n;
-    } else {
-      a.in_full = 1;
-      a.in_sz = a.y_sz;
-      a.in_sy = a.y_sy;
-    }
-    a.f = F;
-    a.w = nullptr;
-    a.y = nullptr;
-    a.write_y = 0;
-    a.qs = qs;
-    rec_begin(st);
-    launch_level<1, TY, TY, TS, TW, PK, QZ>(p, a, st);
-    cudaError_t e = cudaGetLastError();
-    {
-      const Work wk = work_level_load(p, l, false);
-      rec_end(st, "level_load_rec", l, wk.bytes, wk.flops);
-    }
+    cudaError_t e = fork ? cudaStreamWaitEvent(st, fk->ev[l], 0) : load_vector(l, st);
     if (e != cudaSuccess) return e;
-    if ((e = solve_level<TW>(p, l, F, cur, SOLVE_SUB, st)) != cudaSuccess) return e;
+    if ((e = solve_level<TW>(p, l, Fl(l), cur, SOLVE_SUB, st)) != cudaSuccess) return e;
     rec_begin(st);
     if (l == L) {
       launch_interp<TY, TD, TS, TW, PK, QZ>(p, l, cl, cur, out, 1, st, qs);
@@ -306,6 +324,30 @@ cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void
     case kFormF64: return recompose_t<double, double, double, false>(p, in, out, ws, st, all);
     case kFormF32: return recompose_t<float, float, float, false>(p, in, out, ws, st, all);
     default: return recompose_t<float, float, double, false>(p, in, out, ws, st, all);
+  }
+}
+
+cudaError_t enqueue_recompose_fork(const mgr_plan* p, int kind, const void* in, int ncls, const double* bins, void* out,
+                                   void* ws, cudaStream_t st, const ForkCtx& fk) {
+  const ForkCtx* f = &fk;
+  if (kind == 0) {
+    switch (p->form) {
+      case kFormF64: return recompose_t<double, double, double, false>(p, in, out, ws, st, ncls, nullptr, f);
+      case kFormF32: return recompose_t<float, float, float, false>(p, in, out, ws, st, ncls, nullptr, f);
+      default: return recompose_t<float, float, double, false>(p, in, out, ws, st, ncls, nullptr, f);
+    }
+  }
+  if (kind == 1) {
+    switch (p->form) {
+      case kFormF64: return recompose_t<double, double, double, true>(p, in, out, ws, st, ncls, nullptr, f);
+      case kFormF32: return recompose_t<float, float, float, true>(p, in, out, ws, st, ncls, nullptr, f);
+      default: return recompose_t<float, float, double, true>(p, in, out, ws, st, ncls, nullptr, f);
+    }
+  }
+  switch (p->form) {
+    case kFormF64: return recompose_t<double, double, double, true, true>(p, in, out, ws, st, ncls, bins, f);
+    case kFormF32: return recompose_t<float, float, float, true, true>(p, in, out, ws, st, ncls, bins, f);
+    default: return recompose_t<float, float, double, true, true>(p, in, out, ws, st, ncls, bins, f);
   }
 }
 

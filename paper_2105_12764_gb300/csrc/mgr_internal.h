@@ -95,6 +95,11 @@ struct mgr_plan {
   mgr::Tables tables;
   // workspace layout (bytes)
   size_t ws_a = 0, ws_b = 0, ws_f = 0, ws_g = 0, ws_bytes = 0;  // ws_g: 4D time-slice load vectors
+  std::vector<size_t> f_off;  // byte offset of level l's load vector in the F region (l = 1..L)
+  // side stream and events of the forked recomposition graph (created on the
+  // first capture, under graph_mu)
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> fork_ev;
   // launch-sequence cache: one CUDA graph per (op, in, out, workspace)
   std::mutex graph_mu;
   struct GraphEntry {
@@ -148,6 +153,15 @@ cudaError_t enqueue_recompose(const mgr_plan* p, const void* in, void* out, void
 // mgr_st.cu: the 4D (spatiotemporal) form of the two operations
 cudaError_t enqueue_decompose_st(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_st(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
+// A recomposition captured into a graph may run the load-vector passes of all
+// levels on `side`, concurrently with the solve / interpolation chain (they
+// depend only on the coefficients); ev: L + 1 events.
+struct ForkCtx {
+  cudaStream_t side;
+  cudaEvent_t* ev;
+};
+cudaError_t enqueue_recompose_fork(const mgr_plan* p, int op, const void* in, int ncls, const double* bins, void* out,
+                                   void* ws, cudaStream_t st, const ForkCtx& fk);
 // class-packed output / input (recompose from classes 0..ncls-1)
 cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,
