@@ -78,6 +78,8 @@ LevelArgs<TS, TW> level_args(const mgr_plan* p, int l) {
 
 // Number of z chunks for `tiles` xy tiles and mz coarse planes: minimise
 // waves x planes streamed per CTA (each chunk also streams ~1.5 halo planes).
+// Chunks may be a single plane: on small levels the plane loop's latency, not
+// the halo's extra work, bounds the pass, so the more CTAs the better.
 inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_sm) {
   const int64_t slots = int64_t(p->ctx->num_sms) * ctas_per_sm;
   int best = 1;
@@ -85,7 +87,6 @@ inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_
   const int cmax = std::max(1, std::min(mz, 64));
   for (int c = 1; c <= cmax; ++c) {
     const int len = (mz + c - 1) / c;
-    if (c > 1 && len < 4) break;
     const int cc = (mz + len - 1) / len;
     const int64_t waves = (tiles * cc + slots - 1) / slots;
     const double cost = double(waves) * (len + 1.5);
