@@ -110,7 +110,7 @@ int mgr_plan_destroy(mgr_plan* plan);
 /* Depth the plan runs (levels = -1 resolved). */
 int mgr_plan_levels(const mgr_plan* plan, int* levels);
 /* Bytes of device workspace one mgr_decompose / mgr_recompose call needs
-   (coarse-grid buffers: about 0.27 x the field's element count, in the
+   (coarse-grid buffers: about 0.28 x the field's element count, in the
    solve precision).  May be 0 when levels = 0. */
 int mgr_workspace_size(const mgr_plan* plan, size_t* bytes);
 
