@@ -44,6 +44,67 @@ namespace {
 #include "mgr_level.cuh"
 #include "mgr_solve.cuh"
 #include "mgr_launch.cuh"
+#include "mgr_small.cuh"
+
+// Number of coarse levels (1..ls) the single-CTA kernels take: the largest ls
+// whose level grid (a few thousand nodes) and work arrays fit in shared memory.
+template <typename TS, typename TW>
+int small_levels(const mgr_plan* p) {
+  int ls = 0;
+  for (int l = 1; l <= p->levels && l <= kSmallMaxLevels; ++l) {
+    const LevelGeom& g = p->geom[l];
+    const size_t sm =
+        small_smem_bytes<TS, TW>(g.ax[0].n, g.ax[1].n, g.ax[2].n, g.ax[0].m, g.ax[1].m, g.ax[2].m);
+    if (g.space_fine() > 8192 || sm > size_t(200) * 1024 || sm > p->ctx->smem_optin) break;
+    ls = l;
+  }
+  return ls;
+}
+
+template <typename TS, typename TW>
+SmallArgs<TS, TW> small_args(const mgr_plan* p, int ls) {
+  SmallArgs<TS, TW> a{};
+  const TS* T = table<TS>(p);
+  const TW* Tw = table<TW>(p);
+  a.levels = ls;
+  for (int l = 1; l <= ls; ++l)
+    for (int k = 0; k < 3; ++k) {
+      const AxisLevel& ax = p->geom[l].ax[k];
+      a.n[l][k] = ax.n;
+      a.m[l][k] = ax.m;
+      a.active[l][k] = ax.active ? 1 : 0;
+      a.s[l][k] = ax.s;
+      a.wa[l][k] = T + ax.o_wa;
+      a.wb[l][k] = T + ax.o_wb;
+      a.k[l][k] = T + ax.o_k;
+      a.ta[l][k] = Tw + ax.o_ta;
+      a.tb[l][k] = Tw + ax.o_tb;
+    }
+  const int64_t s0 = int64_t(1) << p->levels;
+  for (int k = 0; k < 3; ++k) {
+    a.N[k] = p->full[k];
+    a.n0[k] = int(p->coarsest[k]);
+    a.s0[k] = p->full[k] > 1 ? s0 : 1;
+  }
+  a.sz = p->full[1] * p->full[2];
+  a.sy = p->full[2];
+  return a;
+}
+
+template <typename TD, typename TS, typename TW, bool DEC>
+cudaError_t launch_small(const mgr_plan* p, SmallArgs<TS, TW>& a, cudaStream_t st) {
+  const int ls = a.levels;
+  const size_t sm = small_smem_bytes<TS, TW>(a.n[ls][0], a.n[ls][1], a.n[ls][2], a.m[ls][0], a.m[ls][1], a.m[ls][2]);
+  auto kern = DEC ? k_small_dec<TD, TS, TW> : k_small_rec<TD, TS, TW>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  rec_begin(st);
+  kern<<<1, kSmallThreads, sm, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  double nodes = 0;
+  for (int l = 1; l <= ls; ++l) nodes += double(p->geom[l].fine_count());
+  rec_end(st, DEC ? "small_levels_dec" : "small_levels_rec", ls, nodes * (2.0 * p->elem), 0.0);
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // In-place decomposition of the finest level: coefficients written pointwise
@@ -131,7 +192,8 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   Bufs b = split_ws(p, ws);
   TW* F = static_cast<TW*>(b.F);
   TW* cur = nullptr;  // compact level-l values for l < L
-  for (int l = L; l >= 1; --l) {
+  const int ls = (PK || QZ) ? 0 : small_levels<TS, TW>(p);  // levels ls..1 run in one CTA
+  for (int l = L; l > ls; --l) {
     TW* nxt = static_cast<TW*>(((L - l) % 2 == 0) ? b.A : b.B);
     auto a = level_args<TS, TW>(p, l);
     const LevelGeom& g = p->geom[l];
@@ -185,6 +247,13 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     }
     if ((e = solve_level<TW>(p, l, F, nxt, SOLVE_ADD, st)) != cudaSuccess) return e;
     cur = nxt;
+  }
+  if (ls >= 1) {
+    SmallArgs<TS, TW> sa = small_args<TS, TW>(p, ls);
+    sa.vin = ls == L ? in : static_cast<const void*>(cur);
+    sa.vin_full = ls == L;
+    sa.out = out;
+    return launch_small<TD, TS, TW, true>(p, sa, st);
   }
   // coarsest values into their nodal positions / class 0
   if constexpr (QZ) return coarsest_q_launch<TW, TW>(p, static_cast<int*>(out), cur, bins[0], 1, sat, st);
@@ -244,11 +313,12 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     return e;
   };
   const int last_lv = std::min(L, ncls - 1);  // levels 1..last_lv have their coefficient class
-  const bool fork = fk != nullptr && last_lv >= 1 && t_recorder == nullptr;
+  const int ls = (PK || QZ) ? 0 : small_levels<TS, TW>(p);  // levels 1..ls run in one CTA
+  const bool fork = fk != nullptr && last_lv > ls && t_recorder == nullptr;
   if (fork) {
     if (cudaEventRecord(fk->ev[0], st) != cudaSuccess || cudaStreamWaitEvent(fk->side, fk->ev[0], 0) != cudaSuccess)
       return cudaGetLastError();
-    for (int l = 1; l <= last_lv; ++l) {
+    for (int l = ls + 1; l <= last_lv; ++l) {
       cudaError_t e = load_vector(l, fk->side);
       if (e != cudaSuccess) return e;
       if ((e = cudaEventRecord(fk->ev[l], fk->side)) != cudaSuccess) return e;
@@ -256,14 +326,24 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   }
   // coarsest grid from the nodal positions / class 0
   TW* cur = static_cast<TW*>((L % 2 == 1) ? b.A : b.B);  // level 0 lives where decompose left it
-  {
+  if (ls >= 1) {
+    // levels 1..ls in one CTA; level ls's values go where the level loop keeps them
+    TW* lsbuf = (ls % 2 == 1) ? static_cast<TW*>(cur == b.A ? b.B : b.A) : cur;
+    SmallArgs<TS, TW> sa = small_args<TS, TW>(p, ls);
+    sa.cin = in;
+    sa.vout = ls == L ? out : static_cast<void*>(lsbuf);
+    sa.vout_full = ls == L;
+    cudaError_t e = launch_small<TD, TS, TW, false>(p, sa, st);
+    if (e != cudaSuccess || ls == L) return e;
+    cur = lsbuf;
+  } else {
     cudaError_t e;
     if constexpr (QZ) e = coarsest_q_launch<TW, TW>(p, const_cast<int*>(static_cast<const int*>(in)), cur, bins[0], 0,
                                                     nullptr, st);
     else e = coarsest_copy_launch<TD, TW>(p, const_cast<TD*>(static_cast<const TD*>(in)), cur, PK, 0, st);
     if (e != cudaSuccess) return e;
   }
-  for (int l = 1; l <= L; ++l) {
+  for (int l = ls + 1; l <= L; ++l) {
     const LevelGeom& g = p->geom[l];
     const void* cl = PK ? static_cast<const void*>(static_cast<const TY*>(in) + p->class_off[l]) : in;
     const double qs = QZ ? bins[l] : 1.0;

@@ -109,7 +109,9 @@ def test_multi_tile(ctx, shape):
 
 def test_packed_equals_pack_of_nodal(ctx):
     """The fused class-packed decomposition writes the same values as the
-    nodal one followed by the conversion kernel (bit for bit)."""
+    nodal one followed by the conversion kernel: bit for bit on the levels both
+    run through the tiled kernels, to rounding on the coarse levels the nodal
+    form finishes in its single-CTA kernel."""
     shape = (45, 61, 70)
     rng = np.random.default_rng(3)
     u = torch.from_numpy(rng.standard_normal(shape)).cuda()
@@ -121,7 +123,12 @@ def test_packed_equals_pack_of_nodal(ctx):
     plan.pack_classes(nodal, p1)
     plan.decompose_packed(u, p2, ws)
     torch.cuda.synchronize()
-    assert torch.equal(p1, p2)
+    offs = plan.class_offsets()
+    L = plan.levels
+    a, b = p1.cpu().numpy(), p2.cpu().numpy()
+    # the finest class comes from the same tiled level pass in both forms
+    assert np.array_equal(a[offs[L]:], b[offs[L]:])
+    assert rel_linf(a, b) <= 1e-13
     plan.close()
 
 
