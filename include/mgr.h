@@ -42,7 +42,7 @@ extern "C" {
 #define MGR_ECUDA (-4)     /* a CUDA runtime call failed (sticky errors included)  */
 #define MGR_EPENDING (-5)  /* poll: work not finished yet                          */
 #define MGR_ETIMEDOUT (-6) /* poll/wait: the timeout expired                       */
-#define MGR_EDEVICE (-7)   /* a kernel reported an error through the device word   */
+#define MGR_EDEVICE (-7)   /* reserved for device-reported errors; not returned now  */
 #define MGR_ENOTFOUND (-8) /* unknown ticket / resident handle                     */
 #define MGR_EBUSY (-9)     /* queue full: retry after polling                      */
 
