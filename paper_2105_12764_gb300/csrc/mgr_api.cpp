@@ -4,10 +4,23 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "mgr_internal.h"
+
+namespace mgr {
+
+bool fault_injected(const char* what) {
+  const char* v = std::getenv("MGR_FAULT_INJECT");
+  if (!v || !*v) return false;
+  const std::string list = std::string(",") + v + ",";
+  return list.find(std::string(",") + what + ",") != std::string::npos;
+}
+
+}  // namespace mgr
 
 namespace {
 
@@ -114,6 +127,7 @@ int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cuda
                                         : check_op_args(p, in, out, ws, !packed_op(op));
   if (rc != MGR_OK) return rc;
   if ((rc = check_sticky()) != MGR_OK) return rc;
+  if (mgr::fault_injected("launch")) return MGR_ECUDA;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
   if (cap != cudaStreamCaptureStatusNone) return enqueue(p, op, in, out, ws, st, x) == cudaSuccess ? MGR_OK : MGR_ECUDA;

@@ -748,6 +748,7 @@ int run_group(mgr_ctx* ctx, BatchState& B, const std::vector<const mgr_request*>
     auto e = std::make_unique<BatchState::Entry>();
     e->key = key;
     e->ws_bytes = std::max<size_t>(ws_total, 256);
+    if (fault_injected("alloc")) return MGR_ENOMEM;
     if (cudaMalloc(&e->ws, e->ws_bytes) != cudaSuccess) {
       cudaGetLastError();
       return MGR_ENOMEM;
@@ -839,6 +840,7 @@ int batch_submit(mgr_ctx* ctx, const mgr_request* reqs, int n, uint64_t* ticket)
     else if (r.op == 1) rec.push_back(&r);
     else return MGR_EINVAL;
   }
+  if (fault_injected("launch")) return MGR_ECUDA;
   int rc = MGR_OK;
   for (int pass = 0; pass < 2 && rc == MGR_OK; ++pass) {
     auto& grp = pass == 0 ? dec : rec;

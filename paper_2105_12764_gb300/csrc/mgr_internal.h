@@ -137,6 +137,13 @@ Work work_level_load(const mgr_plan* p, int l, bool decompose);
 Work work_solve(const mgr_plan* p, int l, int axis, bool final_op);
 Work work_interp(const mgr_plan* p, int l);
 
+// Host-side fault injection for tests (no GPU fault is involved): true when
+// the comma-separated list in the environment variable MGR_FAULT_INJECT
+// names `what` ("alloc": device allocations of the batch / serving layers
+// fail; "launch": operations fail before any kernel is launched; "admit":
+// serving admission refuses requests).  Read on every call.
+bool fault_injected(const char* what);
+
 // mgr_plan.cpp
 int build_plan_tables(mgr_plan* p);
 int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default_levels);

@@ -147,7 +147,9 @@ bool admit_one(mgr_server* s) {
   cudaStream_t st = s->streams[si];
   r->stream = si;
   int rc = MGR_OK;
-  if (ws && cudaMallocAsync(&r->ws, ws, st) != cudaSuccess) rc = MGR_ENOMEM;
+  if (mgr::fault_injected("admit")) rc = MGR_EBUDGET;
+  else if (mgr::fault_injected("alloc")) rc = MGR_ENOMEM;
+  if (rc == MGR_OK && ws && cudaMallocAsync(&r->ws, ws, st) != cudaSuccess) rc = MGR_ENOMEM;
   r->ws_bytes = r->ws ? ws : 0;
   s->used += r->ws_bytes;
   const void* src = r->r.in;
@@ -167,6 +169,7 @@ bool admit_one(mgr_server* s) {
   } else if (rc == MGR_OK) {
     src = s->hiers[r->r.src].buf;  // pinned at enqueue, so still resident
   }
+  if (rc == MGR_OK && mgr::fault_injected("launch")) rc = MGR_ECUDA;
   if (rc == MGR_OK) {
     cudaError_t e = r->r.op == MGR_OP_DECOMPOSE ? mgr::enqueue_decompose(p, src, dst, r->ws, st)
                                                 : mgr::enqueue_recompose(p, src, dst, r->ws, st);
