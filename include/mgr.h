@@ -68,7 +68,9 @@ typedef enum {
    layout; the class-packed, quantized and batched forms are 1D-3D only. */
 typedef struct {
   int ndim;                /* 1..4                                                   */
-  int64_t shape[4];        /* shape[0..ndim-1], each >= 2; shape[ndim-1] fastest     */
+  int64_t shape[4];        /* shape[0..ndim-1], each >= 2 and <= 2^30; shape[ndim-1]
+                              fastest; shape[ndim-2] * shape[ndim-1] < 2^31 (and, for
+                              4D, shape[1] * shape[2] * shape[3] < 2^31)              */
   const double* coords[4]; /* HOST, strictly increasing, length shape[k]; NULL means
                               uniform unit spacing x_i = i.  Copied at plan time;
                               spacings are formed in FP64 on the host.               */

@@ -45,6 +45,11 @@ int resolve_levels(const mgr_desc* d, int* levels, int* max_levels, int* default
     mx = std::min(mx, levels_until(d->shape[k], 2));
     df = std::min(df, levels_until(d->shape[k], 3));
   }
+  // the kernels address within a plane of the two fastest axes (and, for 4D,
+  // within a time slice) with 32-bit offsets
+  const int64_t plane = d->ndim >= 2 ? d->shape[d->ndim - 1] * d->shape[d->ndim - 2] : d->shape[0];
+  if (plane >= (int64_t(1) << 31)) return MGR_EINVAL;
+  if (d->ndim == 4 && d->shape[1] * plane >= (int64_t(1) << 31)) return MGR_EINVAL;
   if (max_levels) *max_levels = mx;
   if (default_levels) *default_levels = df;
   if (levels) {

@@ -64,6 +64,12 @@ def test_host_only_entry_points(lib_path):
         assert mgr.default_levels(shape) == oracle.default_levels(shape)
     with pytest.raises(mgr.MgrError):
         mgr.max_levels((1, 5))
+    # planes of 2^31 nodes or more are refused (32-bit in-plane offsets)
+    assert mgr.max_levels((3, 46340, 46340)) == 1
+    for shape in [(2, 46341, 46341), (65536, 32768), (5, 2048, 1024, 1024)]:
+        with pytest.raises(mgr.MgrError) as ei:
+            mgr.max_levels(shape)
+        assert ei.value.code == mgr.MGR_EINVAL
 
 
 def test_no_device_fails_loudly(lib_path):
