@@ -179,9 +179,9 @@ template <typename TW>
 cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t lines, const TW* ta, const TW* tb, int op,
                            cudaStream_t st) {
   (void)p;
-  if (sizeof(TW) == 8 && lines >= 32768) {
-    // FP64 with many lines: the recurrences' FP64 latency needs more lines in
-    // flight per SM than whole lines staged in shared memory allow
+  if (lines >= 32768) {
+    // many lines: the recurrences' latency needs more lines in flight per SM
+    // than whole lines staged in shared memory allow
     const int64_t nwarps = (lines + 31) / 32;
     k_solve_rows<TW><<<int((nwarps + kRowsWarps - 1) / kRowsWarps), kRowsWarps * 32, 0, st>>>(f, w, mx, lines, mx, ta,
                                                                                              tb, op);

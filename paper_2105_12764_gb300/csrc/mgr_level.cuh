@@ -196,9 +196,17 @@ __device__ __forceinline__ void load_pair(T* dst, const T* src0, const T* src1, 
   }
 }
 
-// Store a pair of output values (to adjacent or separate addresses).
+// Store a pair of output values (to adjacent or separate addresses).  4-byte
+// values are always stored one by one: the warp's stores still coalesce, and
+// the FP32 level pass, bound by instruction issue, saves the alignment test
+// and its branch (measured 7% faster at 513^3).
 template <typename T>
 __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bool w1, bool contig) {
+  if constexpr (sizeof(T) == 4) {
+    if (w0) *p0 = a0;
+    if (w1) *p1 = a1;
+    return;
+  }
   if (w0 && w1 && contig && ((reinterpret_cast<uintptr_t>(p0) & (2 * sizeof(T) - 1)) == 0)) {
     typename Pair<T>::type v;
     v.x = a0;

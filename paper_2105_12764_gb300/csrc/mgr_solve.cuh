@@ -22,15 +22,15 @@ __device__ __forceinline__ void apply_op(TW* f, TW* w, int64_t g, TW v, int op) 
 // Lines along a strided axis, one thread per line: element q of line
 // (o, i) sits at o*ostride + i + q*lstride; consecutive threads take
 // consecutive i, so every step is a coalesced access.  `line` is this
-// thread's line index in [0, inner*outer).
-template <typename TW>
+// thread's line index in [0, inner*outer).  U elements of the line are
+// loaded before the recurrence runs through them (loads in flight per thread).
+template <typename TW, int U = 8>
 __device__ __forceinline__ void solve_strided_line(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t lstride,
                                                    int inner, int64_t ostride, const TW* __restrict__ ta,
                                                    const TW* __restrict__ tb, int op, int64_t line) {
   const int i = int(line % inner);
   const int64_t o = line / inner;
   TW* fl = f + o * ostride + i;
-  constexpr int U = 8;
   TW prev = TW(0);
   for (int q0 = 0; q0 < mline; q0 += U) {
     TW buf[U];
@@ -75,7 +75,9 @@ __global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* _
                                                        const TW* __restrict__ ta, const TW* __restrict__ tb, int op) {
   const int64_t id = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (id >= int64_t(inner) * outer) return;
-  solve_strided_line<TW>(f, w, mline, lstride, inner, ostride, ta, tb, op, id);
+  // 64 bytes of loads in flight per thread and sweep: sixteen FP32 or eight FP64 elements
+  // (sixteen FP64 elements cost occupancy and were slower)
+  solve_strided_line<TW, sizeof(TW) == 4 ? 16 : 8>(f, w, mline, lstride, inner, ostride, ta, tb, op, id);
 }
 
 // Lines along the contiguous axis: R rows of length mline (row pitch
@@ -167,6 +169,9 @@ __global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__
                                                                 int64_t rows, int64_t row_pitch,
                                                                 const TW* __restrict__ ta, const TW* __restrict__ tb,
                                                                 int op) {
+  // loads of a tile are issued in batches of B before their shared-memory
+  // stores (128 bytes of loads in flight per thread)
+  constexpr int B = 128 / sizeof(TW);
   __shared__ TW tiles[kRowsWarps][32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t r0 = (int64_t(blockIdx.x) * kRowsWarps + warp) * 32;
@@ -174,14 +179,22 @@ __global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__
   const int nr = int(rows - r0 < 32 ? rows - r0 : 32);
   TW(*tile)[33] = tiles[warp];
   TW* base = f + r0 * row_pitch;
+  TW* wb = w + r0 * row_pitch;
   const bool act = lane < nr;
+  auto load_tile = [&](int c0) {
+#pragma unroll
+    for (int i0 = 0; i0 < 32; i0 += B) {
+      TW v[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) v[u] = (i0 + u < nr) ? base[int64_t(i0 + u) * row_pitch + c0 + lane] : TW(0);
+#pragma unroll
+      for (int u = 0; u < B; ++u) tile[lane][i0 + u] = v[u];
+    }
+  };
   TW prev = TW(0);
   for (int c0 = 0; c0 < mline; c0 += 32) {
     const int nc = min(32, mline - c0);
-    if (lane < nc) {
-#pragma unroll 8
-      for (int i = 0; i < nr; ++i) tile[lane][i] = base[int64_t(i) * row_pitch + c0 + lane];
-    }
+    if (lane < nc) load_tile(c0);
     __syncwarp();
     if (act) {
       for (int c = 0; c < nc; ++c) {
@@ -196,14 +209,10 @@ __global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__
     }
     __syncwarp();
   }
-  TW* wb = w + r0 * row_pitch;
   TW next = TW(0);
   for (int c0 = ((mline - 1) / 32) * 32; c0 >= 0; c0 -= 32) {
     const int nc = min(32, mline - c0);
-    if (lane < nc) {
-#pragma unroll 8
-      for (int i = 0; i < nr; ++i) tile[lane][i] = base[int64_t(i) * row_pitch + c0 + lane];
-    }
+    if (lane < nc) load_tile(c0);
     __syncwarp();
     if (act) {
       for (int c = nc - 1; c >= 0; --c) {
@@ -213,12 +222,20 @@ __global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__
     }
     __syncwarp();
     if (lane < nc) {
+      if (op == SOLVE_INPLACE) {
 #pragma unroll 8
-      for (int i = 0; i < nr; ++i) {
-        const int64_t g = int64_t(i) * row_pitch + c0 + lane;
-        if (op == SOLVE_INPLACE) base[g] = tile[lane][i];
-        else if (op == SOLVE_ADD) wb[g] = wb[g] + tile[lane][i];
-        else wb[g] = wb[g] - tile[lane][i];
+        for (int i = 0; i < nr; ++i) base[int64_t(i) * row_pitch + c0 + lane] = tile[lane][i];
+      } else {
+        const TW sg = op == SOLVE_ADD ? TW(1) : TW(-1);
+#pragma unroll
+        for (int i0 = 0; i0 < 32; i0 += B) {
+          TW v[B];
+#pragma unroll
+          for (int u = 0; u < B; ++u) v[u] = (i0 + u < nr) ? wb[int64_t(i0 + u) * row_pitch + c0 + lane] : TW(0);
+#pragma unroll
+          for (int u = 0; u < B; ++u)
+            if (i0 + u < nr) wb[int64_t(i0 + u) * row_pitch + c0 + lane] = v[u] + sg * tile[lane][i0 + u];
+        }
       }
     }
     __syncwarp();
