@@ -40,7 +40,7 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-classes", action="store_true")
     ap.add_argument("--no-st", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
@@ -80,7 +81,7 @@ def path_bytes(shape, levels, elem):
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -96,7 +97,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -206,13 +207,13 @@ def core_source_hash():
 
 # ---------------------------------------------------------------- our arm ---
 
-def time_form(mgr, ctx, u_np, dtype, prec, steps, warmup, ws, sampler=None):
+def time_form(mgr, ctx, u_np, dtype, prec, steps, warmup, ws, sampler=None, coords=None):
     import numpy as np
     import torch
 
     td = torch.float64 if dtype == mgr.MGR_F64 else torch.float32
     nd = np.float64 if dtype == mgr.MGR_F64 else np.float32
-    plan = mgr.Plan(ctx, u_np.shape, None, -1, dtype, prec)
+    plan = mgr.Plan(ctx, u_np.shape, coords, -1, dtype, prec)
     x = torch.from_numpy(np.ascontiguousarray(u_np, dtype=nd)).cuda()
     y = torch.empty_like(x)
     z = torch.empty_like(x)
@@ -366,6 +367,9 @@ def run_ours(args):
             del b2
             torch.cuda.empty_cache()
         result["forms"] = forms
+    # ---- the small uniform and the stretched non-uniform workloads
+    if not args.no_configs:
+        result["configs"] = configs_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup, ws)
     # ---- class-packed layout and progressive recomposition (same FP64 field)
     if not args.no_classes:
         result["classes"] = classes_section(mgr, ctx, u, max(3, min(args.steps, 20)), args.warmup, t_dec + t_rec)
@@ -383,6 +387,41 @@ def run_ours(args):
     ctx.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
+
+
+def configs_section(mgr, ctx, steps, warmup, ws):
+    """The 65^3 FP64 sines-plus-noise field, and the 1000x700x300 field on
+    geometrically stretched coordinates (ratio 1.01 per cell) in the mixed,
+    FP32 and FP64 forms: decompose + recompose per step, same metric as the
+    headline (field bytes of the form's element type)."""
+    import numpy as np
+    import torch
+
+    from paper_2105_12764_gb300 import synth
+
+    out = {}
+    u1, _ = synth.workload("c1")
+    runs = [("c1_fp64", u1, None, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, max(steps, 50))]
+    u3, c3 = synth.workload("c3")
+    runs += [("c3_mixed", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_MIXED, steps),
+             ("c3_fp32", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_NATIVE, steps),
+             ("c3_fp64", u3, c3, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, steps)]
+    for name, u, coords, dtype, prec, n in runs:
+        ud = u if dtype == mgr.MGR_F64 else u.astype(np.float32)
+        p, b, td, tr, rt, _ = time_form(mgr, ctx, ud, dtype, prec, n, warmup, ws, coords=coords)
+        nb = ud.size * ud.itemsize
+        out[name] = {"value": round(2.0 * nb / ((td + tr) * 1e-3) / 1e9, 3), "unit": UNIT,
+                     "decompose_gbs": round(nb / (td * 1e-3) / 1e9, 3),
+                     "recompose_gbs": round(nb / (tr * 1e-3) / 1e9, 3),
+                     "ms_per_step": round(td + tr, 4), "shape": list(ud.shape), "levels": p.levels,
+                     "round_trip_rel_err": rt}
+        p.close()
+        del b
+        torch.cuda.empty_cache()
+    out["workload"] = ("c1: 65^3 unit spacing, three seeded sines (|k| <= 4) + N(0, 1e-3) noise; "
+                       "c3: 1000x700x300, coordinates stretched by 1.01 per cell on every axis, smooth field + "
+                       "seeded Gaussian bumps (widths 2-20 cells)")
+    return out
 
 
 def classes_section(mgr, ctx, u_np, steps, warmup, nodal_ms):
