@@ -237,11 +237,17 @@ def time_form(mgr, ctx, u_np, dtype, prec, steps, warmup, ws, sampler=None, coor
     torch.cuda.synchronize()
     barrier(ws)
     t1 = time.time()
-    t_dec = sum(a.elapsed_time(b) for a, b, _ in ev) / steps
-    t_rec = sum(b.elapsed_time(c) for _, b, c in ev) / steps
+    dec = [a.elapsed_time(b) for a, b, _ in ev]
+    rec = [b.elapsed_time(c) for _, b, c in ev]
+    t_dec = sum(dec) / steps
+    t_rec = sum(rec) / steps
+    step = [d + r for d, r in zip(dec, rec)]
+    stats = {"step_ms_median": round(statistics.median(step), 4), "step_ms_best": round(min(step), 4),
+             "decompose_ms_median": round(statistics.median(dec), 4),
+             "recompose_ms_median": round(statistics.median(rec), 4)}
     # correctness of what was timed: round trip of the last step
     rt = float((z - x).abs().max().item() / x.abs().max().item())
-    return plan, (x, y, z, wsb), t_dec, t_rec, rt, (t0, t1)
+    return plan, (x, y, z, wsb), t_dec, t_rec, rt, (t0, t1, stats)
 
 
 def run_ours(args):
@@ -260,7 +266,7 @@ def run_ours(args):
     nbytes64 = u.size * 8
     sampler = ClockSampler(local)
     sampler.start()
-    plan, bufs, t_dec, t_rec, rt64, (t0, t1) = time_form(mgr, ctx, u, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, args.steps,
+    plan, bufs, t_dec, t_rec, rt64, (t0, t1, step_stats) = time_form(mgr, ctx, u, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, args.steps,
                                                            args.warmup, ws)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
@@ -280,6 +286,8 @@ def run_ours(args):
         "recompose_gbs": round(nbytes64 / (t_rec * 1e-3) / 1e9, 3),
         "hbm_frac_alg": round(2.0 * alg / ((t_dec + t_rec) * 1e-3) / 1e9 / hbm, 4),
         "round_trip_rel_err": rt64,
+        "step_stats": dict(step_stats, note="value and ms_per_step use the mean step; median and best of the same "
+                                            "timed steps (CUDA events per operation)"),
         "clocks": clocks,
     }
     # ---- per-kernel CUDA-event timing of the same operation (dominant kernel roofline)
