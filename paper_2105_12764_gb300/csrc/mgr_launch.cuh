@@ -179,9 +179,9 @@ template <typename TW>
 cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t lines, const TW* ta, const TW* tb, int op,
                            cudaStream_t st) {
   (void)p;
-  if (lines >= 32768) {
-    // many lines: the recurrences' latency needs more lines in flight per SM
-    // than whole lines staged in shared memory allow
+  if (sizeof(TW) == 8 && lines >= 32768) {
+    // FP64 with many lines: the recurrences' FP64 latency needs more lines in
+    // flight per SM than whole lines staged in shared memory allow
     const int64_t nwarps = (lines + 31) / 32;
     k_solve_rows<TW><<<int((nwarps + kRowsWarps - 1) / kRowsWarps), kRowsWarps * 32, 0, st>>>(f, w, mx, lines, mx, ta,
                                                                                              tb, op);
@@ -236,6 +236,14 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
     mline = mz; lstride = int64_t(my) * mx; inner = mx; outer = my; ostride = mx;
   }
   const int64_t lines = int64_t(inner) * outer;
+  const size_t ssm = solve_staged_smem<TW>(mline);
+  if (lines < 32768 && ssm <= size_t(100) * 1024 && ssm <= p->ctx->smem_optin) {
+    // few lines (coarse levels): whole lines staged in shared memory, 32 per CTA
+    cudaFuncSetAttribute(k_solve_staged<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ssm));
+    k_solve_staged<TW><<<int((lines + kStagedLines - 1) / kStagedLines), 128, ssm, st>>>(f, w, mline, lstride, inner,
+                                                                                       outer, ostride, ta, tb, op);
+    return cudaGetLastError();
+  }
   const int threads = 128;
   const int blocks = int((lines + threads - 1) / threads);
   k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb, op);

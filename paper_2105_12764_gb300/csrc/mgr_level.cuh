@@ -287,7 +287,6 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const bool owx0 = vx0 && gx0 >= ox0 && gx0 < ox1, owx1 = vx1 && gx1 >= ox0 && gx1 < ox1;
   const int ic0 = a.in_full ? int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])) : gx0;
   const int ic1 = a.in_full ? int(fmap(min(gx1, nx - 1), a.s[2], a.N[2])) : gx1;
-  const bool icontig = ic1 == ic0 + 1;
   const int yc0 = PK ? gx0 : int(fmap(min(gx0, nx - 1), a.s[2], a.N[2]));
   const int yc1 = PK ? gx1 : int(fmap(min(gx1, nx - 1), a.s[2], a.N[2]));
   const bool ycontig = yc1 == yc0 + 1;

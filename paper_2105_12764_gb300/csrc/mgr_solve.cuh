@@ -80,11 +80,118 @@ __global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* _
   solve_strided_line<TW, sizeof(TW) == 4 ? 16 : 8>(f, w, mline, lstride, inner, ostride, ta, tb, op, id);
 }
 
+// Lines along a strided axis, 32 per CTA, staged whole in shared memory: the
+// CTA's lines (consecutive line indices, so each step q is one or two
+// contiguous row segments) are copied in with asynchronous copies all in
+// flight, one warp runs the 32 recurrences on the staged lines, and the CTA
+// writes them back (or applies the correction).  Each element crosses HBM
+// once each way instead of twice, and all of a CTA's loads are in flight at
+// once: the form for coarse levels, whose few lines leave the one-thread-per-
+// line kernel latency-bound.  With many lines the single computing warp per
+// CTA bounds it, and the one-thread-per-line kernel is faster.
+constexpr int kStagedLines = 32;
+
+template <typename TW>
+size_t solve_staged_smem(int mline) {
+  return sizeof(TW) * (size_t(mline) * kStagedLines + 2 * size_t(mline)) + sizeof(int64_t) * kStagedLines;
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_solve_staged(TW* __restrict__ f, TW* __restrict__ w, int mline,
+                                                      int64_t lstride, int inner, int64_t outer, int64_t ostride,
+                                                      const TW* __restrict__ ta, const TW* __restrict__ tb,
+                                                      int op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NL = kStagedLines;
+  TW* s = reinterpret_cast<TW*>(smem_raw);  // [mline][NL]
+  TW* sa = s + int64_t(mline) * NL;           // [mline]
+  TW* sb = sa + mline;                        // [mline]
+  int64_t* off = reinterpret_cast<int64_t*>(sb + mline);  // [NL] offset of each line's first element
+  const int64_t lines = int64_t(inner) * outer;
+  const int64_t l0 = int64_t(blockIdx.x) * NL;
+  const int nl = int(lines - l0 < NL ? lines - l0 : NL);
+  if (threadIdx.x < NL) {
+    const int64_t line = l0 + (threadIdx.x < nl ? threadIdx.x : 0);
+    const int64_t o = line / inner;
+    off[threadIdx.x] = o * ostride + (line - o * inner);
+  }
+  for (int q = threadIdx.x; q < mline; q += blockDim.x) {
+    sa[q] = ta[q];
+    sb[q] = tb[q];
+  }
+  __syncthreads();
+  const int total = mline * NL;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int q = e / NL, j = e - q * NL;
+    if (j < nl) cp_async(s + e, f + off[j] + int64_t(q) * lstride, int(sizeof(TW)));
+  }
+  cp_commit();
+  cp_wait<0>();
+  __syncthreads();
+  if (threadIdx.x < nl) {
+    const int j = threadIdx.x;
+    constexpr int U = 8;
+    TW prev = TW(0);
+    for (int q0 = 0; q0 < mline; q0 += U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q0 + u < mline) ? s[(q0 + u) * NL + j] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        prev = v[u] - sa[min(q0 + u, mline - 1)] * prev;
+        v[u] = prev;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q0 + u < mline) s[(q0 + u) * NL + j] = v[u];
+    }
+    TW next = TW(0);
+    for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
+      TW v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = (q1 - u >= 0) ? s[(q1 - u) * NL + j] : TW(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        next = v[u] - sb[max(q1 - u, 0)] * next;
+        v[u] = next;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q1 - u >= 0) s[(q1 - u) * NL + j] = v[u];
+    }
+  }
+  __syncthreads();
+  constexpr int W = 8;
+  for (int e0 = threadIdx.x; e0 < total; e0 += W * blockDim.x) {
+    int64_t g[W];
+    TW sv[W], wv[W];
+    bool ok[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int ee = e < total ? e : 0;
+      const int q = ee / NL, j = ee - q * NL;
+      ok[u] = e < total && j < nl;
+      g[u] = off[j] + int64_t(q) * lstride;
+      sv[u] = s[ee];
+      wv[u] = (op != SOLVE_INPLACE && ok[u]) ? w[g[u]] : TW(0);
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      if (!ok[u]) continue;
+      if (op == SOLVE_INPLACE) f[g[u]] = sv[u];
+      else if (op == SOLVE_ADD) w[g[u]] = wv[u] + sv[u];
+      else w[g[u]] = wv[u] - sv[u];
+    }
+  }
+}
+
 // Lines along the contiguous axis: R rows of length mline (row pitch
 // row_pitch) starting at row r0 are staged in shared memory with coalesced
-// loads/stores by all threads; thread r < R then runs its row's recurrences
-// in register chunks of 8 (eight independent loads, eight dependent FMAs,
-// eight stores).  The recurrence coefficients are staged once.
+// asynchronous copies by all threads; thread r < R then runs its row's
+// recurrences in register chunks of 8 (eight independent loads, eight
+// dependent FMAs, eight stores), and all threads write the rows back.  The
+// recurrence coefficients are staged once.
 template <typename TW>
 __device__ __forceinline__ size_t solve_contig_smem(int mline, int R) {
   return sizeof(TW) * (size_t(R) * (mline | 1) + 2 * size_t(mline));
@@ -100,14 +207,19 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
   TW* sa = s + R * pitch;                   // [mline]
   TW* sb = sa + mline;                      // [mline]
   const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
+  const int total = nr * mline;
+  // the rows go to shared memory as element-wise asynchronous copies, all in
+  // flight at once (the staging, not the recurrences, bounds this kernel)
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = e / mline, c = e - r * mline;
+    cp_async(s + r * pitch + c, f + (r0 + r) * row_pitch + c, int(sizeof(TW)));
+  }
+  cp_commit();
   for (int q = threadIdx.x; q < mline; q += blockDim.x) {
     sa[q] = ta[q];
     sb[q] = tb[q];
   }
-  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
-    const int r = e / mline, c = e - r * mline;
-    s[r * pitch + c] = f[(r0 + r) * row_pitch + c];
-  }
+  cp_wait<0>();
   __syncthreads();
   if (threadIdx.x < nr) {
     TW* l = s + threadIdx.x * pitch;
@@ -142,9 +254,27 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nr * mline; e += blockDim.x) {
-    const int r = e / mline, c = e - r * mline;
-    apply_op<TW>(f, w, (r0 + r) * row_pitch + c, s[r * pitch + c], op);
+  // write back (or apply the correction to w), W elements per thread per
+  // round with their loads of w issued together
+  constexpr int W = 8;
+  for (int e0 = threadIdx.x; e0 < total; e0 += W * blockDim.x) {
+    int64_t g[W];
+    TW sv[W], wv[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int r = (e < total ? e : 0) / mline, c = (e < total ? e : 0) - r * mline;
+      g[u] = (r0 + r) * row_pitch + c;
+      sv[u] = s[r * pitch + c];
+      wv[u] = (op != SOLVE_INPLACE && e < total) ? w[g[u]] : TW(0);
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      if (e0 + u * blockDim.x >= total) break;
+      if (op == SOLVE_INPLACE) f[g[u]] = sv[u];
+      else if (op == SOLVE_ADD) w[g[u]] = wv[u] + sv[u];
+      else w[g[u]] = wv[u] - sv[u];
+    }
   }
 }
 
