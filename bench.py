@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-classes", action="store_true")
     ap.add_argument("--no-st", action="store_true")
-    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
@@ -375,9 +375,9 @@ def run_ours(args):
             del b2
             torch.cuda.empty_cache()
         result["forms"] = forms
-    # ---- the small uniform and the stretched non-uniform workloads
-    if not args.no_configs:
-        result["configs"] = configs_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup, ws)
+    # ---- the 65^3 sines field and the stretched 1000x700x300 field
+    if not args.no_workloads:
+        result["workloads"] = workloads_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup, ws)
     # ---- class-packed layout and progressive recomposition (same FP64 field)
     if not args.no_classes:
         result["classes"] = classes_section(mgr, ctx, u, max(3, min(args.steps, 20)), args.warmup, t_dec + t_rec)
@@ -397,7 +397,7 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
 
 
-def configs_section(mgr, ctx, steps, warmup, ws):
+def workloads_section(mgr, ctx, steps, warmup, ws):
     """The 65^3 FP64 sines-plus-noise field, and the 1000x700x300 field on
     geometrically stretched coordinates (ratio 1.01 per cell) in the mixed,
     FP32 and FP64 forms: decompose + recompose per step, same metric as the
@@ -408,12 +408,12 @@ def configs_section(mgr, ctx, steps, warmup, ws):
     from paper_2105_12764_gb300 import synth
 
     out = {}
-    u1, _ = synth.workload("c1")
-    runs = [("c1_fp64", u1, None, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, max(steps, 50))]
-    u3, c3 = synth.workload("c3")
-    runs += [("c3_mixed", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_MIXED, steps),
-             ("c3_fp32", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_NATIVE, steps),
-             ("c3_fp64", u3, c3, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, steps)]
+    u1, _ = synth.workload("sines65")
+    runs = [("sines_65^3_fp64", u1, None, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, max(steps, 50))]
+    u3, c3 = synth.workload("bumps_stretched_1000x700x300")
+    runs += [("stretched_1000x700x300_mixed", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_MIXED, steps),
+             ("stretched_1000x700x300_fp32", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_NATIVE, steps),
+             ("stretched_1000x700x300_fp64", u3, c3, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, steps)]
     for name, u, coords, dtype, prec, n in runs:
         ud = u if dtype == mgr.MGR_F64 else u.astype(np.float32)
         p, b, td, tr, rt, _ = time_form(mgr, ctx, ud, dtype, prec, n, warmup, ws, coords=coords)
@@ -426,9 +426,9 @@ def configs_section(mgr, ctx, steps, warmup, ws):
         p.close()
         del b
         torch.cuda.empty_cache()
-    out["workload"] = ("c1: 65^3 unit spacing, three seeded sines (|k| <= 4) + N(0, 1e-3) noise; "
-                       "c3: 1000x700x300, coordinates stretched by 1.01 per cell on every axis, smooth field + "
-                       "seeded Gaussian bumps (widths 2-20 cells)")
+    out["workload"] = ("sines: 65^3 unit spacing, three seeded sines (|k| <= 4) + N(0, 1e-3) noise; "
+                       "stretched: 1000x700x300, coordinates stretched by 1.01 per cell on every axis, smooth "
+                       "field + seeded Gaussian bumps (widths 2-20 cells)")
     return out
 
 
@@ -558,7 +558,7 @@ def batched_section(mgr, ctx, steps):
 
     from paper_2105_12764_gb300 import synth
 
-    specs = synth.c4_field_specs(4096, seed=0)
+    specs = synth.batch_field_specs(4096, seed=0)
     plans32, plans64, x32, y32, z32 = [], [], [], [], []
     elems = 0
     for i, (shape, st) in enumerate(specs):

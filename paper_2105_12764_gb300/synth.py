@@ -6,14 +6,18 @@ values, so seeded synthetic fields of the same shapes stand in for it.  This
 module only generates inputs (fields and coordinates); it contains none of the
 decomposition's arithmetic and serves both the CUDA path and the CPU oracle.
 
-Workloads
-  C1  65^3 FP64, unit spacing: sum of three seeded sines with random wave
-      vectors |k| <= 4 cycles per domain plus N(0, 1e-3) noise.
-  C2  513^3 (2^9+1, Sec. IV.B's kernel size): Gaussian random field with power
-      spectrum |k|^-5/3 synthesised by FFT, normalised to mean 0 / variance 1.
-  C3  1000 x 700 x 300 (not 2^k+1), geometric coordinates h_i = 1.01^i per
-      axis: smooth low-frequency product of cosines plus 32 Gaussian bumps
-      (centres uniform in index space, widths 2..20 cells, N(0,1) amplitudes).
+Workloads (by name)
+  sines65       65^3 FP64, unit spacing: sum of three seeded sines with random
+                wave vectors |k| <= 4 cycles per domain plus N(0, 1e-3) noise.
+  grf513        513^3 (2^9+1, Sec. IV.B's kernel size): Gaussian random field
+                with power spectrum |k|^-5/3 synthesised by FFT, normalised to
+                mean 0 / variance 1.
+  bumps_stretched_1000x700x300
+                1000 x 700 x 300 (not 2^k+1), geometric coordinates
+                h_i = 1.01^i per axis: smooth low-frequency product of cosines
+                plus 32 Gaussian bumps (centres uniform in index space, widths
+                2..20 cells, N(0,1) amplitudes).
+  batch_field_specs: 4096 uneven 2D / 3D fields for the batched form.
 """
 import numpy as np
 
@@ -43,7 +47,7 @@ def stretched_coords(n, ratio=1.01, h0=1.0):
 
 
 def sines_field(shape, seed=0, n_waves=3, kmax=4.0, noise=1e-3):
-    """C1: sum of seeded sines, wave vectors uniform in the ball |k| <= kmax."""
+    """Sum of seeded sines, wave vectors uniform in the ball |k| <= kmax."""
     rng = np.random.default_rng(seed)
     d = len(shape)
     grids = np.meshgrid(*[np.arange(n, dtype=np.float64) / (n - 1) for n in shape], indexing="ij")
@@ -60,7 +64,7 @@ def sines_field(shape, seed=0, n_waves=3, kmax=4.0, noise=1e-3):
 
 
 def grf_field(shape, seed=0, slope=-5.0 / 3.0):
-    """C2: Gaussian random field with power |k|^slope (amplitude |k|^(slope/2))."""
+    """Gaussian random field with power |k|^slope (amplitude |k|^(slope/2))."""
     rng = np.random.default_rng(seed)
     white = rng.standard_normal(shape)
     spec = _rfftn(white)
@@ -89,7 +93,7 @@ def grf_field(shape, seed=0, slope=-5.0 / 3.0):
 
 
 def bumps_field(shape, seed=0, n_bumps=32, coords=None):
-    """C3: smooth product of cosines over normalised coordinates plus Gaussian bumps."""
+    """Smooth product of cosines over normalised coordinates plus Gaussian bumps."""
     rng = np.random.default_rng(seed)
     d = len(shape)
     if coords is None:
@@ -129,9 +133,9 @@ def bumps_field(shape, seed=0, n_bumps=32, coords=None):
 
 
 WORKLOADS = {
-    "c1": dict(shape=(65, 65, 65), dtype="f64", coords="uniform"),
-    "c2": dict(shape=(513, 513, 513), dtype="f64", coords="uniform"),
-    "c3": dict(shape=(1000, 700, 300), dtype="f32", coords="stretched"),
+    "sines65": dict(shape=(65, 65, 65), dtype="f64", coords="uniform"),
+    "grf513": dict(shape=(513, 513, 513), dtype="f64", coords="uniform"),
+    "bumps_stretched_1000x700x300": dict(shape=(1000, 700, 300), dtype="f32", coords="stretched"),
 }
 
 
@@ -139,19 +143,19 @@ def workload(name, seed=0, shape=None):
     """(field, coords) of a named workload; coords is None for unit spacing."""
     spec = WORKLOADS[name]
     shape = tuple(shape) if shape is not None else spec["shape"]
-    if name == "c1":
+    if name == "sines65":
         return sines_field(shape, seed), None
-    if name == "c2":
+    if name == "grf513":
         return grf_field(shape, seed), None
     coords = [stretched_coords(n) for n in shape]
     return bumps_field(shape, seed, coords=coords), coords
 
 
 # ---------------------------------------------------------------------------
-# C4: thousands of uneven fields for the batched form
+# thousands of uneven fields for the batched form
 # ---------------------------------------------------------------------------
 
-def c4_field_specs(count=4096, seed=0):
+def batch_field_specs(count=4096, seed=0):
     """(shape, stretched) of the batched workload.
 
     Element count N is log-uniform on [17^2, 129^3]; N <= 129^2 gives a

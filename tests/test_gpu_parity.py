@@ -111,10 +111,10 @@ def test_inplace(ctx):
     check_f64(ctx, u, coords, inplace=True)
 
 
-def test_c1_workload(ctx):
+def test_sines65_workload(ctx):
     from paper_2105_12764_gb300 import synth
 
-    u, coords = synth.workload("c1")
+    u, coords = synth.workload("sines65")
     check_f64(ctx, u, coords)
 
 

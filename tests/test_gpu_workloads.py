@@ -1,9 +1,9 @@
 """Full-size parity: the bench workloads through the C ABI vs the FP64 oracle.
 
-C2: 513^3 k^-5/3 field, full hierarchy (8 levels), in the launch
-configuration bench.py times (same plan, graph-replayed launches):
-  FP64 vs oracle <= 1e-12, round trip <= 1e-13; FP32 and mixed <= 1e-5.
-C3: 1000 x 700 x 300 stretched (1.01 per cell), mixed precision <= 1e-5.
+513^3 k^-5/3 field, full hierarchy (8 levels), in the launch configuration
+bench.py times (same plan, graph-replayed launches): FP64 vs oracle <= 1e-12,
+round trip <= 1e-13; FP32 and mixed <= 1e-5.
+1000 x 700 x 300 stretched (1.01 per cell), mixed precision <= 1e-5.
 Every output element is compared (the oracle computes the whole field).
 """
 import numpy as np
@@ -26,33 +26,33 @@ def ctx():
 
 
 @pytest.fixture(scope="module")
-def c2_field():
+def grf513_field():
     from paper_2105_12764_gb300 import synth
 
-    return synth.workload("c2")[0]
+    return synth.workload("grf513")[0]
 
 
 @pytest.fixture(scope="module")
-def c2_oracle(c2_field):
-    return oracle.decompose(c2_field)
+def grf513_oracle(grf513_field):
+    return oracle.decompose(grf513_field)
 
 
-def test_c2_fp64_full(ctx, c2_field, c2_oracle):
-    r = Runner(ctx, c2_field.shape, None, -1, mgr.MGR_F64)
+def test_grf513_fp64_full(ctx, grf513_field, grf513_oracle):
+    r = Runner(ctx, grf513_field.shape, None, -1, mgr.MGR_F64)
     try:
-        got = r.decompose(c2_field)
-        assert rel_linf(got, c2_oracle) <= 1e-12
+        got = r.decompose(grf513_field)
+        assert rel_linf(got, grf513_oracle) <= 1e-12
         back = r.recompose(got)
-        assert rel_linf(back, c2_field) <= 1e-13
+        assert rel_linf(back, grf513_field) <= 1e-13
     finally:
         r.close()
 
 
 @pytest.mark.parametrize("prec", [mgr.MGR_PREC_NATIVE, mgr.MGR_PREC_MIXED])
-def test_c2_fp32_forms_full(ctx, c2_field, prec):
-    u32 = c2_field.astype(np.float32)
+def test_grf513_fp32_forms_full(ctx, grf513_field, prec):
+    u32 = grf513_field.astype(np.float32)
     ref = oracle.decompose(u32.astype(np.float64))
-    r = Runner(ctx, c2_field.shape, None, -1, mgr.MGR_F32, prec)
+    r = Runner(ctx, grf513_field.shape, None, -1, mgr.MGR_F32, prec)
     try:
         got = r.decompose(u32)
         err = rel_linf(got, ref)
@@ -63,10 +63,10 @@ def test_c2_fp32_forms_full(ctx, c2_field, prec):
         r.close()
 
 
-def test_c3_mixed_full(ctx):
+def test_stretched_1000x700x300_mixed_full(ctx):
     from paper_2105_12764_gb300 import synth
 
-    u, coords = synth.workload("c3")
+    u, coords = synth.workload("bumps_stretched_1000x700x300")
     u32 = u.astype(np.float32)
     del u
     ref = oracle.decompose(u32.astype(np.float64), coords)
@@ -82,24 +82,24 @@ def test_c3_mixed_full(ctx):
         r.close()
 
 
-def test_c2_fp64_class_packed_and_progressive_full(ctx, c2_field, c2_oracle):
+def test_grf513_fp64_class_packed_and_progressive_full(ctx, grf513_field, grf513_oracle):
     """The class-packed form at the bench size: equal to the oracle's classes; every
     class recomposes the field; class 0 alone gives the coarsest interpolant."""
-    shape = c2_field.shape
+    shape = grf513_field.shape
     plan = mgr.Plan(ctx, shape, None, -1, mgr.MGR_F64)
     L = plan.levels
-    x = torch.from_numpy(c2_field).cuda()
+    x = torch.from_numpy(grf513_field).cuda()
     pk = torch.empty(x.numel(), dtype=x.dtype, device="cuda")
     y = torch.empty_like(x)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     try:
         plan.decompose_packed(x, pk, ws)
         torch.cuda.synchronize()
-        want = oracle.pack_classes(c2_oracle, L)
+        want = oracle.pack_classes(grf513_oracle, L)
         assert rel_linf(pk.cpu().numpy(), want) <= 1e-12
         plan.recompose_packed(pk, L + 1, y, ws)
         torch.cuda.synchronize()
-        assert rel_linf(y.cpu().numpy(), c2_field) <= 1e-13
+        assert rel_linf(y.cpu().numpy(), grf513_field) <= 1e-13
         # prefix of the first L classes (finest class dropped), against the oracle on
         # its own classes
         plan.recompose_packed(pk, L, y, ws)
@@ -110,16 +110,16 @@ def test_c2_fp64_class_packed_and_progressive_full(ctx, c2_field, c2_oracle):
         plan.close()
 
 
-def test_c2_fp64_quantized_full(ctx, c2_field):
+def test_grf513_fp64_quantized_full(ctx, grf513_field):
     """Fused quantization at the bench size: the recomposed field is within tau."""
-    plan = mgr.Plan(ctx, c2_field.shape, None, -1, mgr.MGR_F64)
-    x = torch.from_numpy(c2_field).cuda()
+    plan = mgr.Plan(ctx, grf513_field.shape, None, -1, mgr.MGR_F64)
+    x = torch.from_numpy(grf513_field).cuda()
     codes = torch.empty(x.numel(), dtype=torch.int32, device="cuda")
     y = torch.empty_like(x)
     sat = torch.zeros(1, dtype=torch.int64, device="cuda")
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     try:
-        span = float(c2_field.max() - c2_field.min())
+        span = float(grf513_field.max() - grf513_field.min())
         for rel in (1e-2, 1e-5):
             tau = rel * span
             plan.decompose_quantized(x, codes, tau, ws, sat)
