@@ -44,7 +44,8 @@ int check_sticky() {
 
 // Operation codes of run_op / the graph cache; OP_REC_PACKED and OP_REC_DEQ
 // carry the number of classes in bits 8 and up.
-enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3, OP_DEC_QUANT = 4, OP_REC_DEQ = 5 };
+enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3, OP_DEC_QUANT = 4, OP_REC_DEQ = 5,
+       OP_DEC_HOST = 6 /* graph-cache key of the pipelined host-buffer decomposition */ };
 
 // Arguments of the quantized operations (part of the graph-cache key).
 struct Extra {
@@ -162,10 +163,84 @@ int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cuda
   return cudaGraphLaunch(exec, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
 }
 
+// page-locked (or registered) host memory
+bool host_pinned(const void* ptr) {
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeHost;
+}
+
+// Decomposition with pinned host buffers as one cached graph: copies in by
+// slabs, the finest level pass in parts as the slabs arrive, the finished
+// planes copied back while the coarser levels run (mgr::PipeCtx).
+int run_host_pipe(mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
+                  cudaStream_t st) {
+  int rc = check_op_args(p, dev_in, dev_out, ws, false);
+  if (rc != MGR_OK) return rc;
+  if ((rc = check_sticky()) != MGR_OK) return rc;
+  if (mgr::fault_injected("launch")) return MGR_ECUDA;
+  std::lock_guard<std::mutex> lk(p->graph_mu);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : p->graphs)
+    if (g.op == OP_DEC_HOST && g.in == host_in && g.out == host_out && g.ws == ws && g.din == dev_in &&
+        g.dout == dev_out)
+      exec = g.exec;
+  if (!exec) {
+    if (!p->pipe_h2d) {
+      if (cudaStreamCreateWithFlags(&p->pipe_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&p->pipe_d2h, cudaStreamNonBlocking) != cudaSuccess)
+        return MGR_ECUDA;
+      p->pipe_ev.assign(mgr::kPipeEvents, nullptr);
+      for (auto& e : p->pipe_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MGR_ECUDA;
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MGR_ECUDA;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = mgr::enqueue_decompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs,
+                                                        mgr::PipeCtx{p->pipe_h2d, p->pipe_d2h, p->pipe_ev.data()});
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return MGR_ECUDA;
+    }
+    if (p->graphs.size() >= 8) {
+      cudaGraphExecDestroy(p->graphs.front().exec);
+      p->graphs.erase(p->graphs.begin());
+    }
+    mgr_plan::GraphEntry ge{OP_DEC_HOST, host_in, host_out, ws, 0.0, nullptr, exec};
+    ge.din = dev_in;
+    ge.dout = dev_out;
+    p->graphs.push_back(ge);
+  }
+  return cudaGraphLaunch(exec, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+}
+
 int run_host(const mgr_plan* p, int op, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
              cudaStream_t st) {
   if (!p || !host_in || !host_out || !dev_in || !dev_out) return MGR_EINVAL;
   const size_t bytes = size_t(p->count) * p->elem;
+  if (op == OP_DEC && (host_in == host_out || !ranges_overlap(host_in, bytes, host_out, bytes)) &&
+      mgr::pipe_eligible(p, dev_in, dev_out) && host_pinned(host_in) && host_pinned(host_out)) {
+    // a decomposition that can overlap its copies with its kernels (the input
+    // planes a part of the finest level reads are always copied in before any
+    // plane is copied back, so host_out may alias host_in exactly); not while
+    // the caller's stream is being captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
+    if (cap == cudaStreamCaptureStatusNone)
+      return run_host_pipe(const_cast<mgr_plan*>(p), host_in, host_out, dev_in, dev_out, ws, st);
+  }
   if (cudaMemcpyAsync(dev_in, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return MGR_ECUDA;
   int rc = run_op(p, op, dev_in, dev_out, ws, st);
   if (rc != MGR_OK) return rc;
@@ -343,6 +418,9 @@ int mgr_plan_destroy(mgr_plan* p) {
     p->graphs.clear();
     for (cudaEvent_t e : p->fork_ev) cudaEventDestroy(e);
     if (p->side) cudaStreamDestroy(p->side);
+    for (cudaEvent_t e : p->pipe_ev) cudaEventDestroy(e);
+    if (p->pipe_h2d) cudaStreamDestroy(p->pipe_h2d);
+    if (p->pipe_d2h) cudaStreamDestroy(p->pipe_d2h);
   }
   cudaFree(p->tables.d64);
   cudaFree(p->tables.d32);

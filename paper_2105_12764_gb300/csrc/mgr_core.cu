@@ -167,13 +167,25 @@ cudaError_t coarsest_q_launch(const mgr_plan* p, int* codes, TV* v, double q, in
   return e;
 }
 
+// The finest level pass of a pipelined host-buffer decomposition: part k
+// covers the pass's z chunks [c0[k], c0[k+1]), waits for wait[k] (its input
+// planes are on the device) and records done[k].
+struct PipeParts {
+  int parts;
+  const int* c0;
+  const cudaEvent_t* wait;
+  const cudaEvent_t* done;
+};
+
 // PK: write the coefficients in the class-packed layout (class l at
 // p->class_off[l]; `out` must not overlap `in`).  QZ (with PK): write int32
 // codes with the bin widths bins[0..L] instead, counting saturated codes in
-// *sat (when not null).
+// *sat (when not null).  pp: run the finest level pass in parts (nodal, out
+// of place, finest level tiled).
 template <typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st,
-                        const double* bins = nullptr, unsigned long long* sat = nullptr) {
+                        const double* bins = nullptr, unsigned long long* sat = nullptr,
+                        const PipeParts* pp = nullptr) {
   static_assert(PK || !QZ, "quantized output is class-packed");
   using TY = std::conditional_t<QZ, int, TD>;  // coefficient output type
   const int L = p->levels;
@@ -216,7 +228,15 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
       a.in_full = 1;
       a.in_sz = p->full[1] * p->full[2];
       a.in_sy = p->full[2];
-      launch_level<0, TD, TY, TS, TW, PK, QZ>(p, a, st);
+      if (pp) {
+        for (int k = 0; k < pp->parts; ++k) {
+          if (cudaStreamWaitEvent(st, pp->wait[k], 0) != cudaSuccess) return cudaGetLastError();
+          launch_level_chunks<0, TD, TY, TS, TW, PK, QZ>(p, a, pp->c0[k], pp->c0[k + 1], st);
+          if (cudaEventRecord(pp->done[k], st) != cudaSuccess) return cudaGetLastError();
+        }
+      } else {
+        launch_level<0, TD, TY, TS, TW, PK, QZ>(p, a, st);
+      }
     } else {
       a.in = cur;
       a.in_full = 0;
@@ -386,7 +406,96 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   return cudaSuccess;
 }
 
+template <typename TD, typename TS, typename TW>
+bool pipe_eligible_t(const mgr_plan* p) {
+  const int L = p->levels;
+  return L >= 1 && small_levels<TS, TW>(p) < L;
+}
+
+// Pipelined decomposition with host buffers (see PipeCtx).  Part k of the
+// finest level pass covers coarse z planes [qz0, qz1); it reads level planes
+// up to p(min(qz1, mz-1)) and finishes the planes 2t-1, t in (qz0, qz1],
+// that are fine in z.
+template <typename TD, typename TS, typename TW>
+cudaError_t host_pipe_t(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in, void* dev_out,
+                        void* ws, cudaStream_t st, const PipeCtx& pc) {
+  const int L = p->levels;
+  const int nz = int(p->full[0]), mz = p->geom[L].ax[0].m;
+  const size_t plane = size_t(p->full[1]) * size_t(p->full[2]) * sizeof(TD);
+  auto a = level_args<TS, TW>(p, L);
+  const dim3 grid = level_grid(p, a);
+  const int gz = int(grid.z), qc = a.qz_chunk;
+  const int parts = std::min(gz, kPipeParts);
+  int c0[kPipeParts + 1];
+  for (int k = 0; k <= parts; ++k) c0[k] = int((int64_t(k) * gz) / parts);
+  // events: [0] start, [1 .. kPipeParts] slabs copied, [kPipeParts+1 .. 2 kPipeParts] parts done,
+  // [2 kPipeParts+1] operation done, [2 kPipeParts+2] copies back done
+  cudaEvent_t* h2d_ev = pc.ev + 1;
+  cudaEvent_t* done_ev = pc.ev + 1 + kPipeParts;
+  const cudaEvent_t end_ev = pc.ev[2 * kPipeParts + 1], back_ev = pc.ev[2 * kPipeParts + 2];
+  const char* hin = static_cast<const char*>(host_in);
+  char* hout = static_cast<char*>(host_out);
+  char* din = static_cast<char*>(const_cast<void*>(dev_in));
+  char* dout = static_cast<char*>(dev_out);
+  cudaError_t e;
+  if ((e = cudaEventRecord(pc.ev[0], st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(pc.h2d, pc.ev[0], 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(pc.d2h, pc.ev[0], 0)) != cudaSuccess) return e;
+  int next = 0;  // first plane not yet copied in
+  for (int k = 0; k < parts; ++k) {
+    const int qz1 = std::min(c0[k + 1] * qc, mz);
+    const int hi = (k == parts - 1) ? nz - 1 : std::min(2 * std::min(qz1, mz - 1), nz - 1);
+    if (hi >= next) {
+      if ((e = cudaMemcpyAsync(din + size_t(next) * plane, hin + size_t(next) * plane, size_t(hi - next + 1) * plane,
+                               cudaMemcpyHostToDevice, pc.h2d)) != cudaSuccess)
+        return e;
+      next = hi + 1;
+    }
+    if ((e = cudaEventRecord(h2d_ev[k], pc.h2d)) != cudaSuccess) return e;
+  }
+  const PipeParts pp{parts, c0, h2d_ev, done_ev};
+  if ((e = decompose_t<TD, TS, TW, false>(p, dev_in, dev_out, ws, st, nullptr, nullptr, &pp)) != cudaSuccess) return e;
+  for (int k = 0; k < parts; ++k) {
+    if ((e = cudaStreamWaitEvent(pc.d2h, done_ev[k], 0)) != cudaSuccess) return e;
+    const int qz0 = c0[k] * qc, qz1 = std::min(c0[k + 1] * qc, mz);
+    const int t0 = qz0 + 1, t1 = std::min(std::min(qz1, mz - 1), (nz - 1) / 2);
+    if (t1 >= t0 &&
+        (e = cudaMemcpy2DAsync(hout + size_t(2 * t0 - 1) * plane, 2 * plane, dout + size_t(2 * t0 - 1) * plane,
+                               2 * plane, plane, size_t(t1 - t0 + 1), cudaMemcpyDeviceToHost, pc.d2h)) != cudaSuccess)
+      return e;
+  }
+  // the even planes, and the last plane when it has an odd index (it is coarse)
+  if ((e = cudaEventRecord(end_ev, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(pc.d2h, end_ev, 0)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy2DAsync(hout, 2 * plane, dout, 2 * plane, plane, size_t((nz + 1) / 2), cudaMemcpyDeviceToHost,
+                             pc.d2h)) != cudaSuccess)
+    return e;
+  if (nz % 2 == 0 && (e = cudaMemcpyAsync(hout + size_t(nz - 1) * plane, dout + size_t(nz - 1) * plane, plane,
+                                          cudaMemcpyDeviceToHost, pc.d2h)) != cudaSuccess)
+    return e;
+  if ((e = cudaEventRecord(back_ev, pc.d2h)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(st, back_ev, 0);
+}
+
 }  // namespace
+
+bool pipe_eligible(const mgr_plan* p, const void* dev_in, const void* dev_out) {
+  if (!p || p->desc.ndim != 3 || dev_in == dev_out || p->levels < 1 || p->full[0] < 32) return false;
+  switch (p->form) {
+    case kFormF64: return pipe_eligible_t<double, double, double>(p);
+    case kFormF32: return pipe_eligible_t<float, float, float>(p);
+    default: return pipe_eligible_t<float, float, double>(p);
+  }
+}
+
+cudaError_t enqueue_decompose_host_pipe(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
+                                        void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc) {
+  switch (p->form) {
+    case kFormF64: return host_pipe_t<double, double, double>(p, host_in, host_out, dev_in, dev_out, ws, st, pc);
+    case kFormF32: return host_pipe_t<float, float, float>(p, host_in, host_out, dev_in, dev_out, ws, st, pc);
+    default: return host_pipe_t<float, float, double>(p, host_in, host_out, dev_in, dev_out, ws, st, pc);
+  }
+}
 
 cudaError_t enqueue_decompose(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st) {
   if (p->desc.ndim == 4) return enqueue_decompose_st(p, in, out, ws, st);

@@ -100,6 +100,10 @@ struct mgr_plan {
   // first capture, under graph_mu)
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> fork_ev;
+  // copy streams and events of the pipelined host-buffer decomposition
+  // (created on its first capture, under graph_mu)
+  cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;
   // launch-sequence cache: one CUDA graph per (op, in, out, workspace)
   std::mutex graph_mu;
   struct GraphEntry {
@@ -110,6 +114,8 @@ struct mgr_plan {
     double tau;   // quantized operations: tolerance
     void* aux;    // quantized decomposition: saturation counter
     cudaGraphExec_t exec;
+    const void* din = nullptr;  // host-buffer operations: the device buffers
+    void* dout = nullptr;
   };
   std::vector<GraphEntry> graphs;
 };
@@ -169,6 +175,24 @@ struct ForkCtx {
 };
 cudaError_t enqueue_recompose_fork(const mgr_plan* p, int op, const void* in, int ncls, const double* bins, void* out,
                                    void* ws, cudaStream_t st, const ForkCtx& fk);
+// Decomposition with pinned host buffers, pipelined (graph capture only): the
+// input planes go to the device in slabs on `h2d`; the finest level pass runs
+// in parts, each as soon as its planes are there; the planes a part finishes
+// that are fine in z (they hold only finest-level coefficients, final once the
+// part is done) go back on `d2h` while the coarser levels run; the other
+// planes follow at the end.  ev: kPipeEvents events.
+constexpr int kPipeParts = 8;
+constexpr int kPipeEvents = 2 * kPipeParts + 3;
+struct PipeCtx {
+  cudaStream_t h2d, d2h;
+  cudaEvent_t* ev;
+};
+// whether a decomposition from host_in into host_out through dev_in / dev_out
+// can run pipelined (3D nodal plan with a tiled finest level, distinct device
+// buffers, enough planes)
+bool pipe_eligible(const mgr_plan* p, const void* dev_in, const void* dev_out);
+cudaError_t enqueue_decompose_host_pipe(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
+                                        void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc);
 // class-packed output / input (recompose from classes 0..ncls-1)
 cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,

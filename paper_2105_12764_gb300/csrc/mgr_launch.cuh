@@ -119,6 +119,23 @@ void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
   kern<<<grid, C::NW * 32, sm, st>>>(a);
 }
 
+// z chunks [c0, c1) of the level pass's grid (the grid level_grid chooses):
+// a level pass may run as several such launches, each as soon as its input
+// planes are ready.
+template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ = false>
+void launch_level_chunks(const mgr_plan* p, LevelArgs<TS, TW>& a, int c0, int c1, cudaStream_t st) {
+  using C = LevelCfg<TS>;
+  constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
+  auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  dim3 grid = level_grid(p, a);
+  if (c1 <= c0 || c1 > int(grid.z)) return;
+  a.bz0 = c0;
+  grid.z = unsigned(c1 - c0);
+  kern<<<grid, C::NW * 32, sm, st>>>(a);
+  a.bz0 = 0;
+}
+
 // c: nodal coefficients (PK false), the packed class of level l (PK true), or
 // null for a dropped class (all coefficients zero); QZ: c holds codes of bin
 // width qs

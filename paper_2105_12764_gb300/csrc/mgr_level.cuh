@@ -160,6 +160,7 @@ struct LevelArgs {
   const TS* wb[3];
   const TS* k[3];
   int qz_chunk;
+  int bz0;         // first z chunk of this launch (a launch may cover a subset of the chunks)
   int write_y;
   double qs;                // QZ: 1/bin width (MODE 0) or bin width (MODE 1)
   unsigned long long* qsat; // QZ, MODE 0: saturated-code counter (may be null)
@@ -683,7 +684,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
