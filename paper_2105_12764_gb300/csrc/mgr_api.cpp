@@ -45,7 +45,7 @@ int check_sticky() {
 // Operation codes of run_op / the graph cache; OP_REC_PACKED and OP_REC_DEQ
 // carry the number of classes in bits 8 and up.
 enum { OP_DEC = 0, OP_REC = 1, OP_DEC_PACKED = 2, OP_REC_PACKED = 3, OP_DEC_QUANT = 4, OP_REC_DEQ = 5,
-       OP_DEC_HOST = 6 /* graph-cache key of the pipelined host-buffer decomposition */ };
+       OP_DEC_HOST = 6, OP_REC_HOST = 7 /* graph-cache keys of the pipelined host-buffer operations */ };
 
 // Arguments of the quantized operations (part of the graph-cache key).
 struct Extra {
@@ -83,18 +83,23 @@ cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* 
 
 bool packed_op(int op) { return (op & 0xff) >= OP_DEC_PACKED; }
 
+// The side stream and events of a forked recomposition graph (graph_mu held).
+bool ensure_fork(mgr_plan* p) {
+  if (p->side) return true;
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return false;
+  p->fork_ev.assign(p->levels + 1, nullptr);
+  for (auto& e : p->fork_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+  return true;
+}
+
 // Enqueue while capturing a graph (graph_mu held): recompositions fork their
 // load-vector passes onto the plan's side stream.
 cudaError_t enqueue_captured(mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t cs, const Extra& x) {
   const int base = op & 0xff;
   const bool rec = base == OP_REC || base == OP_REC_PACKED || base == OP_REC_DEQ;
   if (!rec || p->desc.ndim == 4 || p->levels < 1) return enqueue(p, op, in, out, ws, cs, x);
-  if (!p->side) {
-    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return cudaErrorMemoryAllocation;
-    p->fork_ev.assign(p->levels + 1, nullptr);
-    for (auto& e : p->fork_ev)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cudaErrorMemoryAllocation;
-  }
+  if (!ensure_fork(p)) return cudaErrorMemoryAllocation;
   std::vector<double> bins;
   if (base == OP_REC_DEQ && mgr::quant_bins(p, x.tau, bins) != MGR_OK) return cudaErrorInvalidValue;
   const int ncls = base == OP_REC ? p->levels + 1 : (op >> 8);
@@ -173,11 +178,11 @@ bool host_pinned(const void* ptr) {
   return attr.type == cudaMemoryTypeHost;
 }
 
-// Decomposition with pinned host buffers as one cached graph: copies in by
-// slabs, the finest level pass in parts as the slabs arrive, the finished
-// planes copied back while the coarser levels run (mgr::PipeCtx).
-int run_host_pipe(mgr_plan* p, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
+// A decomposition or recomposition with pinned host buffers as one cached
+// graph whose copies overlap its kernels (mgr::PipeCtx).
+int run_host_pipe(mgr_plan* p, int op, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
                   cudaStream_t st) {
+  const int key = op == OP_DEC ? OP_DEC_HOST : OP_REC_HOST;
   int rc = check_op_args(p, dev_in, dev_out, ws, false);
   if (rc != MGR_OK) return rc;
   if ((rc = check_sticky()) != MGR_OK) return rc;
@@ -185,8 +190,7 @@ int run_host_pipe(mgr_plan* p, const void* host_in, void* host_out, void* dev_in
   std::lock_guard<std::mutex> lk(p->graph_mu);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : p->graphs)
-    if (g.op == OP_DEC_HOST && g.in == host_in && g.out == host_out && g.ws == ws && g.din == dev_in &&
-        g.dout == dev_out)
+    if (g.op == key && g.in == host_in && g.out == host_out && g.ws == ws && g.din == dev_in && g.dout == dev_out)
       exec = g.exec;
   if (!exec) {
     if (!p->pipe_h2d) {
@@ -197,13 +201,17 @@ int run_host_pipe(mgr_plan* p, const void* host_in, void* host_out, void* dev_in
       for (auto& e : p->pipe_ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return MGR_ECUDA;
     }
+    if (op == OP_REC && !ensure_fork(p)) return MGR_ECUDA;
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MGR_ECUDA;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = mgr::enqueue_decompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs,
-                                                        mgr::PipeCtx{p->pipe_h2d, p->pipe_d2h, p->pipe_ev.data()});
+      const mgr::PipeCtx pc{p->pipe_h2d, p->pipe_d2h, p->pipe_ev.data()};
+      cudaError_t e2 =
+          op == OP_DEC ? mgr::enqueue_decompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs, pc)
+                       : mgr::enqueue_recompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs, pc,
+                                                          mgr::ForkCtx{p->side, p->fork_ev.data()});
       e = cudaStreamEndCapture(cs, &graph);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -218,7 +226,7 @@ int run_host_pipe(mgr_plan* p, const void* host_in, void* host_out, void* dev_in
       cudaGraphExecDestroy(p->graphs.front().exec);
       p->graphs.erase(p->graphs.begin());
     }
-    mgr_plan::GraphEntry ge{OP_DEC_HOST, host_in, host_out, ws, 0.0, nullptr, exec};
+    mgr_plan::GraphEntry ge{key, host_in, host_out, ws, 0.0, nullptr, exec};
     ge.din = dev_in;
     ge.dout = dev_out;
     p->graphs.push_back(ge);
@@ -230,16 +238,14 @@ int run_host(const mgr_plan* p, int op, const void* host_in, void* host_out, voi
              cudaStream_t st) {
   if (!p || !host_in || !host_out || !dev_in || !dev_out) return MGR_EINVAL;
   const size_t bytes = size_t(p->count) * p->elem;
-  if (op == OP_DEC && (host_in == host_out || !ranges_overlap(host_in, bytes, host_out, bytes)) &&
+  if ((op == OP_DEC || op == OP_REC) && !ranges_overlap(host_in, bytes, host_out, bytes) &&
       mgr::pipe_eligible(p, dev_in, dev_out) && host_pinned(host_in) && host_pinned(host_out)) {
-    // a decomposition that can overlap its copies with its kernels (the input
-    // planes a part of the finest level reads are always copied in before any
-    // plane is copied back, so host_out may alias host_in exactly); not while
-    // the caller's stream is being captured
+    // an operation that can overlap its copies with its kernels; not while the
+    // caller's stream is being captured
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
     if (cap == cudaStreamCaptureStatusNone)
-      return run_host_pipe(const_cast<mgr_plan*>(p), host_in, host_out, dev_in, dev_out, ws, st);
+      return run_host_pipe(const_cast<mgr_plan*>(p), op, host_in, host_out, dev_in, dev_out, ws, st);
   }
   if (cudaMemcpyAsync(dev_in, host_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return MGR_ECUDA;
   int rc = run_op(p, op, dev_in, dev_out, ws, st);

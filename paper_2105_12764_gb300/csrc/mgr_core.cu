@@ -288,9 +288,25 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
 // fk (graph capture only): the load-vector passes of all levels run on
 // fk->side ahead of the solve / interpolation chain on st, each level into its
 // own load-vector buffer; st waits for level l's before its solves.
+// The recomposition of a pipelined host-buffer call: every pass waits for
+// `even` (the planes holding the coefficients of the coarser levels are on the
+// device); the finest level's load-vector pass runs in parts over its z chunks
+// [c0[k], c0[k+1]), part k after odd[k] (the odd planes it reads); the finest
+// interpolation runs in parts over its z chunks [ic0[k], ic0[k+1]), recording
+// done[k] after part k.
+struct RecPipe {
+  cudaEvent_t even;
+  int parts;
+  const int* c0;
+  const cudaEvent_t* odd;
+  int iparts;
+  const int* ic0;
+  const cudaEvent_t* done;
+};
+
 template <typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st, int ncls,
-                        const double* bins = nullptr, const ForkCtx* fk = nullptr) {
+                        const double* bins = nullptr, const ForkCtx* fk = nullptr, const RecPipe* rp = nullptr) {
   static_assert(PK || !QZ, "quantized input is class-packed");
   using TY = std::conditional_t<QZ, int, TD>;  // coefficient input type
   const int L = p->levels;
@@ -326,7 +342,14 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     a.write_y = 0;
     a.qs = QZ ? bins[l] : 1.0;
     rec_begin(s);
-    launch_level<1, TY, TY, TS, TW, PK, QZ>(p, a, s);
+    if (rp && l == L) {
+      for (int k = 0; k < rp->parts; ++k) {
+        if (cudaStreamWaitEvent(s, rp->odd[k], 0) != cudaSuccess) return cudaGetLastError();
+        launch_level_chunks<1, TY, TY, TS, TW, PK, QZ>(p, a, rp->c0[k], rp->c0[k + 1], s);
+      }
+    } else {
+      launch_level<1, TY, TY, TS, TW, PK, QZ>(p, a, s);
+    }
     cudaError_t e = cudaGetLastError();
     const Work wk = work_level_load(p, l, false);
     rec_end(s, "level_load_rec", l, wk.bytes, wk.flops);
@@ -335,6 +358,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   const int last_lv = std::min(L, ncls - 1);  // levels 1..last_lv have their coefficient class
   const int ls = (PK || QZ) ? 0 : small_levels<TS, TW>(p);  // levels 1..ls run in one CTA
   const bool fork = fk != nullptr && last_lv > ls && t_recorder == nullptr;
+  if (rp && cudaStreamWaitEvent(st, rp->even, 0) != cudaSuccess) return cudaGetLastError();
   if (fork) {
     if (cudaEventRecord(fk->ev[0], st) != cudaSuccess || cudaStreamWaitEvent(fk->side, fk->ev[0], 0) != cudaSuccess)
       return cudaGetLastError();
@@ -389,7 +413,12 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if (e != cudaSuccess) return e;
     if ((e = solve_level<TW>(p, l, Fl(l), cur, SOLVE_SUB, st)) != cudaSuccess) return e;
     rec_begin(st);
-    if (l == L) {
+    if (l == L && rp) {
+      for (int k = 0; k < rp->iparts; ++k) {
+        launch_interp_chunks<TY, TD, TS, TW, PK, QZ>(p, l, cl, cur, out, 1, st, qs, rp->ic0[k], rp->ic0[k + 1]);
+        if (cudaEventRecord(rp->done[k], st) != cudaSuccess) return cudaGetLastError();
+      }
+    } else if (l == L) {
       launch_interp<TY, TD, TS, TW, PK, QZ>(p, l, cl, cur, out, 1, st, qs);
     } else {
       TW* nxt = static_cast<TW*>(cur == b.A ? b.B : b.A);
@@ -477,7 +506,88 @@ cudaError_t host_pipe_t(const mgr_plan* p, const void* host_in, void* host_out, 
   return cudaStreamWaitEvent(st, back_ev, 0);
 }
 
+// Pipelined recomposition with host buffers: the even planes first (they hold
+// every coefficient of the coarser levels, and the last plane of an even
+// plane count), then the odd planes in slabs, each slab releasing a part of
+// the finest load-vector pass; the output planes go back as each part of the
+// finest interpolation finishes (part k writes planes [2 qz0, 2 qz1) , the
+// last part up to the last plane).
+template <typename TD, typename TS, typename TW>
+cudaError_t host_rec_pipe_t(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
+                            void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc, const ForkCtx& fk) {
+  const int L = p->levels;
+  const int nz = int(p->full[0]), mz = p->geom[L].ax[0].m;
+  const size_t plane = size_t(p->full[1]) * size_t(p->full[2]) * sizeof(TD);
+  auto a = level_args<TS, TW>(p, L);
+  const int gz = int(level_grid(p, a).z), qc = a.qz_chunk;
+  const int parts = std::min(gz, kPipeParts);
+  int c0[kPipeParts + 1];
+  for (int k = 0; k <= parts; ++k) c0[k] = int((int64_t(k) * gz) / parts);
+  int gx, gy;
+  auto ia = interp_args<TS, TW, false>(p, L, nullptr, nullptr, nullptr, 1, 1.0, &gx, &gy);
+  const int giz = interp_chunks(p, ia, gx, gy), iqc = ia.qz_chunk;
+  const int iparts = std::min(giz, kPipeParts);
+  int ic0[kPipeParts + 1];
+  for (int k = 0; k <= iparts; ++k) ic0[k] = int((int64_t(k) * giz) / iparts);
+  // events: [0] start, [1] even planes in, [2 .. kPipeParts+1] odd slabs in,
+  // [kPipeParts+2 .. 2 kPipeParts+1] interpolation parts done, [2 kPipeParts+2] copies back done
+  const cudaEvent_t even_ev = pc.ev[1], back_ev = pc.ev[2 * kPipeParts + 2];
+  cudaEvent_t* odd_ev = pc.ev + 2;
+  cudaEvent_t* done_ev = pc.ev + 2 + kPipeParts;
+  const char* hin = static_cast<const char*>(host_in);
+  char* hout = static_cast<char*>(host_out);
+  char* din = static_cast<char*>(const_cast<void*>(dev_in));
+  const char* dout = static_cast<const char*>(dev_out);
+  cudaError_t e;
+  if ((e = cudaEventRecord(pc.ev[0], st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(pc.h2d, pc.ev[0], 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(pc.d2h, pc.ev[0], 0)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy2DAsync(din, 2 * plane, hin, 2 * plane, plane, size_t((nz + 1) / 2), cudaMemcpyHostToDevice,
+                             pc.h2d)) != cudaSuccess)
+    return e;
+  if (nz % 2 == 0 && (e = cudaMemcpyAsync(din + size_t(nz - 1) * plane, hin + size_t(nz - 1) * plane, plane,
+                                          cudaMemcpyHostToDevice, pc.h2d)) != cudaSuccess)
+    return e;
+  if ((e = cudaEventRecord(even_ev, pc.h2d)) != cudaSuccess) return e;
+  int tlo = 1;  // odd planes 2t-1 not yet copied in start at t = tlo
+  for (int k = 0; k < parts; ++k) {
+    const int qz1 = std::min(c0[k + 1] * qc, mz);
+    const int thi = (k == parts - 1) ? (nz - 1) / 2 : std::min(std::min(qz1, mz - 1), (nz - 1) / 2);
+    if (thi >= tlo) {
+      if ((e = cudaMemcpy2DAsync(din + size_t(2 * tlo - 1) * plane, 2 * plane, hin + size_t(2 * tlo - 1) * plane,
+                                 2 * plane, plane, size_t(thi - tlo + 1), cudaMemcpyHostToDevice, pc.h2d)) !=
+          cudaSuccess)
+        return e;
+      tlo = thi + 1;
+    }
+    if ((e = cudaEventRecord(odd_ev[k], pc.h2d)) != cudaSuccess) return e;
+  }
+  const RecPipe rp{even_ev, parts, c0, odd_ev, iparts, ic0, done_ev};
+  if ((e = recompose_t<TD, TS, TW, false>(p, dev_in, dev_out, ws, st, L + 1, nullptr, &fk, &rp)) != cudaSuccess)
+    return e;
+  for (int k = 0; k < iparts; ++k) {
+    if ((e = cudaStreamWaitEvent(pc.d2h, done_ev[k], 0)) != cudaSuccess) return e;
+    const int z0 = 2 * ic0[k] * iqc;
+    const int z1 = (k == iparts - 1) ? nz : std::min(2 * std::min(ic0[k + 1] * iqc, mz), nz);
+    if (z1 > z0 && (e = cudaMemcpyAsync(hout + size_t(z0) * plane, dout + size_t(z0) * plane, size_t(z1 - z0) * plane,
+                                        cudaMemcpyDeviceToHost, pc.d2h)) != cudaSuccess)
+      return e;
+  }
+  if ((e = cudaEventRecord(back_ev, pc.d2h)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(st, back_ev, 0);
+}
+
 }  // namespace
+
+cudaError_t enqueue_recompose_host_pipe(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
+                                        void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc,
+                                        const ForkCtx& fk) {
+  switch (p->form) {
+    case kFormF64: return host_rec_pipe_t<double, double, double>(p, host_in, host_out, dev_in, dev_out, ws, st, pc, fk);
+    case kFormF32: return host_rec_pipe_t<float, float, float>(p, host_in, host_out, dev_in, dev_out, ws, st, pc, fk);
+    default: return host_rec_pipe_t<float, float, double>(p, host_in, host_out, dev_in, dev_out, ws, st, pc, fk);
+  }
+}
 
 bool pipe_eligible(const mgr_plan* p, const void* dev_in, const void* dev_out) {
   if (!p || p->desc.ndim != 3 || dev_in == dev_out || p->levels < 1 || p->full[0] < 32) return false;

@@ -193,6 +193,13 @@ struct PipeCtx {
 bool pipe_eligible(const mgr_plan* p, const void* dev_in, const void* dev_out);
 cudaError_t enqueue_decompose_host_pipe(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
                                         void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc);
+// The recomposition likewise: the coefficients of the coarser levels (the
+// even planes) first, the odd planes in slabs that release parts of the
+// finest load-vector pass (run on fk.side), and the output planes copied back
+// as the parts of the finest interpolation finish.
+cudaError_t enqueue_recompose_host_pipe(const mgr_plan* p, const void* host_in, void* host_out, const void* dev_in,
+                                        void* dev_out, void* ws, cudaStream_t st, const PipeCtx& pc,
+                                        const ForkCtx& fk);
 // class-packed output / input (recompose from classes 0..ncls-1)
 cudaError_t enqueue_decompose_packed(const mgr_plan* p, const void* in, void* out, void* ws, cudaStream_t st);
 cudaError_t enqueue_recompose_packed(const mgr_plan* p, const void* in, int ncls, void* out, void* ws,

@@ -176,18 +176,34 @@ InterpArgs<TS, TW> interp_args(const mgr_plan* p, int l, const void* c, const TW
   return a;
 }
 
-template <typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
-void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st,
-                   double qs) {
-  int gx, gy;
-  InterpArgs<TS, TW> a = interp_args<TS, TW, PK>(p, l, c, w, out, out_full, qs, &gx, &gy);
+// z chunking of an interpolation launch (sets a.qz_chunk; returns the chunk count)
+template <typename TS, typename TW>
+int interp_chunks(const mgr_plan* p, InterpArgs<TS, TW>& a, int gx, int gy) {
   const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
-  const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+  return (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+}
+
+// z chunks [c0, c1) of the interpolation of level l (c1 < 0: all of them)
+template <typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
+void launch_interp_chunks(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full,
+                          cudaStream_t st, double qs, int c0, int c1) {
+  int gx, gy;
+  InterpArgs<TS, TW> a = interp_args<TS, TW, PK>(p, l, c, w, out, out_full, qs, &gx, &gy);
+  const int gz = interp_chunks(p, a, gx, gy);
+  if (c1 < 0) c1 = gz;
+  if (c1 <= c0 || c1 > gz) return;
+  a.bz0 = c0;
   constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
   auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK, QZ>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  kern<<<dim3(gx, gy, gz), kInterpNW * 32, sm, st>>>(a);
+  kern<<<dim3(gx, gy, c1 - c0), kInterpNW * 32, sm, st>>>(a);
+}
+
+template <typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
+void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* out, int out_full, cudaStream_t st,
+                   double qs) {
+  launch_interp_chunks<TD, TO, TS, TW, PK, QZ>(p, l, c, w, out, out_full, st, qs, 0, -1);
 }
 
 // Thomas solves along the contiguous axis: `lines` lines of length mx,

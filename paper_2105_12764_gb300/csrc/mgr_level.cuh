@@ -711,6 +711,7 @@ struct InterpArgs {
   const TS* wa[3];
   const TS* wb[3];
   int qz_chunk;
+  int bz0;    // first z chunk of this launch (a launch may cover a subset of the chunks)
   double qs;  // QZ: bin width of the level's class
 };
 
@@ -913,5 +914,5 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  interp_body<NW, RPW, TD, TO, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+  interp_body<NW, RPW, TD, TO, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0, smem_raw);
 }

@@ -1,11 +1,14 @@
 """Host-buffer entry points (mgr_decompose_host / mgr_recompose_host) against
 the device-buffer operations on the same input.
 
-Pinned host buffers take the pipelined decomposition: the input is copied in
-by slabs of planes, the finest level pass runs in parts as the slabs arrive,
-and the planes a part finishes are copied back while the coarser levels run.
-Pageable buffers, aliased device buffers and small plans take the plain
-copy-compute-copy sequence.  Every path runs the same kernels on the same
+Pinned host buffers take the pipelined operations.  Decomposition: the input
+is copied in by slabs of planes, the finest level pass runs in parts as the
+slabs arrive, and the planes a part finishes are copied back while the
+coarser levels run.  Recomposition: the even planes (every coefficient of the
+coarser levels) first, the odd planes in slabs that release parts of the
+finest load-vector pass, the output copied back part by part behind the
+finest interpolation.  Pageable or aliased host buffers, aliased device
+buffers and small plans take the plain copy-compute-copy sequence.  Every path runs the same kernels on the same
 data, so the host result must equal the device result bit for bit; the host
 output is filled with NaN first, so a plane that is never copied back fails.
 """
@@ -74,9 +77,29 @@ def test_decompose_host_equals_device(ctx, form, shape, pinned):
     plan.close()
 
 
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_recompose_host_equals_device(ctx, form, shape, pinned):
+    dtype, prec, td = FORMS[form]
+    plan = mgr.Plan(ctx, shape, None, -1, dtype, prec)
+    din = torch.empty(shape, dtype=td, device="cuda")
+    dout = torch.empty_like(din)
+    ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device="cuda")
+    for rep in range(3):
+        coef = device_result(plan, field(shape, td, 10 * rep + 2), "dec")
+        hout = torch.full(shape, float("nan"), dtype=td)
+        if pinned:
+            coef, hout = coef.pin_memory(), hout.pin_memory()
+        host_call(plan, "rec", coef, hout, din, dout, ws)
+        want = device_result(plan, coef, "rec")
+        assert torch.equal(hout, want), (form, shape, pinned, rep)
+    plan.close()
+
+
 @pytest.mark.parametrize("form", ["fp64", "fp32"])
 def test_decompose_host_in_place_on_host(ctx, form):
-    """host_out == host_in: every plane is copied in before any is copied back."""
+    """host_out == host_in: the plain sequence."""
     dtype, prec, td = FORMS[form]
     shape = (257, 40, 40)
     plan = mgr.Plan(ctx, shape, None, -1, dtype, prec)
