@@ -348,10 +348,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, ws)
     e_rt = float(np.abs(pin_out.numpy() - u).max() / np.abs(u).max())
+    # the host link's speed on this machine (plain copies of the same buffers), to read the e2e
+    # time against: the step moves the field in and out twice
+    def copy_ms(dst, src):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(3):
+            c0.record(st)
+            dst.copy_(src, non_blocking=True)
+            c1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, c0.elapsed_time(c1))
+        return best
+    h2d_ms, d2h_ms = copy_ms(x, pin_in), copy_ms(pin_out, y)
     result["e2e"] = {"value": round(ws * 2.0 * nbytes64 / (e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
                      "h2d_bytes_per_step": 2 * nbytes64, "d2h_bytes_per_step": 2 * nbytes64,
                      "ms_per_step": round(e_ms, 4), "round_trip_rel_err": e_rt,
-                     "path": "mgr_decompose_host + mgr_recompose_host, pinned host buffers"}
+                     "path": "mgr_decompose_host + mgr_recompose_host, pinned host buffers",
+                     "link": {"h2d_gbs": round(nbytes64 / (h2d_ms * 1e-3) / 1e9, 1),
+                              "d2h_gbs": round(nbytes64 / (d2h_ms * 1e-3) / 1e9, 1),
+                              "copies_back_to_back_ms": round(2.0 * (h2d_ms + d2h_ms), 3),
+                              "note": "one copy of the field each way, best of 3; the step's four copies "
+                                      "back to back would take copies_back_to_back_ms"}}
     del pin_in, pin_c, pin_out
     plan.close()
     del bufs, x, y, z, wsb
