@@ -141,7 +141,12 @@ int mgr_recompose(const mgr_plan* plan, const void* in, void* out, void* workspa
    dev_out back to host_out, all on `stream` (pinned host memory makes the
    copies asynchronous).  dev_in, dev_out: DEVICE, field-sized; they may be
    the same buffer.  Returns after enqueueing; synchronise `stream` before
-   reading host_out. */
+   reading host_out.  With pinned, non-overlapping host buffers, distinct
+   device buffers and a 3D plan of at least 32 planes whose finest level is
+   tiled, the copies overlap the kernels (copies by slabs of planes, the
+   finest level in parts as its planes arrive, finished planes copied back
+   early); the results are the same bits as the plain sequence.  The call
+   takes the plan's graph lock like mgr_decompose. */
 int mgr_decompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
                        void* workspace, mgr_stream_t stream);
 int mgr_recompose_host(const mgr_plan* plan, const void* host_in, void* host_out, void* dev_in, void* dev_out,
