@@ -83,9 +83,10 @@ cudaError_t enqueue(const mgr_plan* p, int op, const void* in, void* out, void* 
 
 bool packed_op(int op) { return (op & 0xff) >= OP_DEC_PACKED; }
 
-// The side stream and events of a forked recomposition graph (graph_mu held).
+// The side streams and events of a forked recomposition graph (graph_mu held).
 bool ensure_fork(mgr_plan* p) {
   if (p->side) return true;
+  if (!p->side2 && cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking) != cudaSuccess) return false;
   if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return false;
   p->fork_ev.assign(p->levels + 1, nullptr);
   for (auto& e : p->fork_ev)
@@ -104,7 +105,7 @@ cudaError_t enqueue_captured(mgr_plan* p, int op, const void* in, void* out, voi
   if (base == OP_REC_DEQ && mgr::quant_bins(p, x.tau, bins) != MGR_OK) return cudaErrorInvalidValue;
   const int ncls = base == OP_REC ? p->levels + 1 : (op >> 8);
   const int kind = base == OP_REC ? 0 : (base == OP_REC_PACKED ? 1 : 2);
-  return mgr::enqueue_recompose_fork(p, kind, in, ncls, bins.data(), out, ws, cs, mgr::ForkCtx{p->side, p->fork_ev.data()});
+  return mgr::enqueue_recompose_fork(p, kind, in, ncls, bins.data(), out, ws, cs, mgr::ForkCtx{p->side, p->fork_ev.data(), p->side2});
 }
 
 // Arguments of a quantized operation: the field (elem bytes per element) and
@@ -211,7 +212,7 @@ int run_host_pipe(mgr_plan* p, int op, const void* host_in, void* host_out, void
       cudaError_t e2 =
           op == OP_DEC ? mgr::enqueue_decompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs, pc)
                        : mgr::enqueue_recompose_host_pipe(p, host_in, host_out, dev_in, dev_out, ws, cs, pc,
-                                                          mgr::ForkCtx{p->side, p->fork_ev.data()});
+                                                          mgr::ForkCtx{p->side, p->fork_ev.data(), p->side2});
       e = cudaStreamEndCapture(cs, &graph);
       if (e2 != cudaSuccess) e = e2;
     }
@@ -424,6 +425,7 @@ int mgr_plan_destroy(mgr_plan* p) {
     p->graphs.clear();
     for (cudaEvent_t e : p->fork_ev) cudaEventDestroy(e);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->side2) cudaStreamDestroy(p->side2);
     for (cudaEvent_t e : p->pipe_ev) cudaEventDestroy(e);
     if (p->pipe_h2d) cudaStreamDestroy(p->pipe_h2d);
     if (p->pipe_d2h) cudaStreamDestroy(p->pipe_d2h);

@@ -286,8 +286,9 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
 // elements are read) and must not overlap `out`.
 // QZ (with PK): `in` holds int32 codes with the bin widths bins[0..L].
 // fk (graph capture only): the load-vector passes of all levels run on
-// fk->side ahead of the solve / interpolation chain on st, each level into its
-// own load-vector buffer; st waits for level l's before its solves.
+// fk->side (the finest level's on fk->side2) ahead of the solve /
+// interpolation chain on st, each level into its own load-vector buffer; st
+// waits for level l's before its solves.
 // The recomposition of a pipelined host-buffer call: every pass waits for
 // `even` (the planes holding the coefficients of the coarser levels are on the
 // device); the finest level's load-vector pass runs in parts over its z chunks
@@ -362,7 +363,16 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   if (fork) {
     if (cudaEventRecord(fk->ev[0], st) != cudaSuccess || cudaStreamWaitEvent(fk->side, fk->ev[0], 0) != cudaSuccess)
       return cudaGetLastError();
-    for (int l = ls + 1; l <= last_lv; ++l) {
+    // the finest level's pass (most of the work, needed last) on its own
+    // stream from the start, the coarser levels' passes in chain order on the other
+    const bool finest_apart = fk->side2 != nullptr && last_lv == L && L > ls + 1;
+    if (finest_apart) {
+      if (cudaStreamWaitEvent(fk->side2, fk->ev[0], 0) != cudaSuccess) return cudaGetLastError();
+      cudaError_t e = load_vector(L, fk->side2);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(fk->ev[L], fk->side2)) != cudaSuccess) return e;
+    }
+    for (int l = ls + 1; l <= (finest_apart ? L - 1 : last_lv); ++l) {
       cudaError_t e = load_vector(l, fk->side);
       if (e != cudaSuccess) return e;
       if ((e = cudaEventRecord(fk->ev[l], fk->side)) != cudaSuccess) return e;

@@ -98,7 +98,7 @@ struct mgr_plan {
   std::vector<size_t> f_off;  // byte offset of level l's load vector in the F region (l = 1..L)
   // side stream and events of the forked recomposition graph (created on the
   // first capture, under graph_mu)
-  cudaStream_t side = nullptr;
+  cudaStream_t side = nullptr, side2 = nullptr;
   std::vector<cudaEvent_t> fork_ev;
   // copy streams and events of the pipelined host-buffer decomposition
   // (created on its first capture, under graph_mu)
@@ -172,6 +172,7 @@ cudaError_t enqueue_recompose_st(const mgr_plan* p, const void* in, void* out, v
 struct ForkCtx {
   cudaStream_t side;
   cudaEvent_t* ev;
+  cudaStream_t side2;  // the finest level's pass (may be null: everything on side)
 };
 cudaError_t enqueue_recompose_fork(const mgr_plan* p, int op, const void* in, int ncls, const double* bins, void* out,
                                    void* ws, cudaStream_t st, const ForkCtx& fk);
