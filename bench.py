@@ -174,10 +174,37 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def make_field(shape, seed):
-    from paper_2105_12764_gb300 import synth
+def synth_module():
+    """The seeded input generators, loaded by file path: importing them through
+    the package would load libmgr.so, which the reference (CPU oracle) arm must
+    not do."""
+    import importlib.util
 
-    return synth.grf_field(shape, seed)
+    name = "_mgr_synth_inputs"
+    if name not in sys.modules:
+        spec = importlib.util.spec_from_file_location(name, os.path.join(ROOT, "paper_2105_12764_gb300", "synth.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        sys.modules[name] = mod
+    return sys.modules[name]
+
+
+def make_field(shape, seed):
+    return synth_module().grf_field(shape, seed)
+
+
+def host_cores():
+    """Cores of this host (os.cpu_count) and the CPU model from lscpu, if present."""
+    info = {"host_cores": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "Thread(s) per core", "Core(s) per socket", "Socket(s)"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
 
 
 def traffic_for(kernel, shape_key, src_hash):
@@ -270,6 +297,10 @@ def run_ours(args):
                                                            args.warmup, ws)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
+    # GPU results kept for the oracle comparison of the CPU-baseline leg (rank 0, N = 1)
+    keep = {} if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
+    if keep is not None:
+        keep["C2 fp64"] = bufs[1].cpu().numpy()
     step_ms = max_over_ranks(t_dec + t_rec, ws)
     value = ws * 2.0 * nbytes64 / (step_ms * 1e-3) / 1e9
     L = plan.levels
@@ -382,6 +413,8 @@ def run_ours(args):
                                               max(3, args.steps), args.warmup, ws)
             nb = u.size * 4
             alg4 = path_bytes(shape, p2.levels, 4)
+            if keep is not None:
+                keep[f"C2 {name}"] = b2[1].cpu().numpy()
             forms[name] = {"value": round(2.0 * nb / ((td + tr) * 1e-3) / 1e9, 3), "unit": UNIT,
                            "decompose_gbs": round(nb / (td * 1e-3) / 1e9, 3),
                            "recompose_gbs": round(nb / (tr * 1e-3) / 1e9, 3),
@@ -395,7 +428,7 @@ def run_ours(args):
         result["forms"] = forms
     # ---- the 65^3 sines field and the stretched 1000x700x300 field
     if not args.no_workloads:
-        result["workloads"] = workloads_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup, ws)
+        result["workloads"] = workloads_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup, ws, keep)
     # ---- class-packed layout and progressive recomposition (same FP64 field)
     if not args.no_classes:
         result["classes"] = classes_section(mgr, ctx, u, max(3, min(args.steps, 20)), args.warmup, t_dec + t_rec)
@@ -404,18 +437,18 @@ def run_ours(args):
         result["spatiotemporal"] = st_section(mgr, ctx, max(3, min(args.steps, 20)), args.warmup)
     # ---- batched form (4096 uneven fields) and served form (Poisson request stream)
     if not args.no_batch:
-        result["batched"] = batched_section(mgr, ctx, max(2, min(args.steps, 10)))
+        result["batched"] = batched_section(mgr, ctx, max(2, min(args.steps, 10)), keep)
     if not args.no_serve:
-        result["served"] = serving_section(mgr, local, args.serve_requests)
+        result["served"] = serving_section(mgr, local, args.serve_requests, keep)
     # ---- CPU baseline: the FP64 oracle, single thread, on rank 0 at N = 1
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(u)
+    if keep is not None:
+        result["cpu_baseline"] = cpu_baseline(u, keep)
     ctx.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
 
 
-def workloads_section(mgr, ctx, steps, warmup, ws):
+def workloads_section(mgr, ctx, steps, warmup, ws, keep=None):
     """The 65^3 FP64 sines-plus-noise field, and the 1000x700x300 field on
     geometrically stretched coordinates (ratio 1.01 per cell) in the mixed,
     FP32 and FP64 forms: decompose + recompose per step, same metric as the
@@ -423,18 +456,20 @@ def workloads_section(mgr, ctx, steps, warmup, ws):
     import numpy as np
     import torch
 
-    from paper_2105_12764_gb300 import synth
+    synth = synth_module()
 
     out = {}
     u1, _ = synth.workload("sines65")
-    runs = [("sines_65^3_fp64", u1, None, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, max(steps, 50))]
+    runs = [("sines_65^3_fp64", u1, None, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, max(steps, 50), "C1 fp64")]
     u3, c3 = synth.workload("bumps_stretched_1000x700x300")
-    runs += [("stretched_1000x700x300_mixed", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_MIXED, steps),
-             ("stretched_1000x700x300_fp32", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_NATIVE, steps),
-             ("stretched_1000x700x300_fp64", u3, c3, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, steps)]
-    for name, u, coords, dtype, prec, n in runs:
+    runs += [("stretched_1000x700x300_mixed", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_MIXED, steps, "C3 mixed"),
+             ("stretched_1000x700x300_fp32", u3, c3, mgr.MGR_F32, mgr.MGR_PREC_NATIVE, steps, "C3 fp32"),
+             ("stretched_1000x700x300_fp64", u3, c3, mgr.MGR_F64, mgr.MGR_PREC_NATIVE, steps, "C3 fp64")]
+    for name, u, coords, dtype, prec, n, kname in runs:
         ud = u if dtype == mgr.MGR_F64 else u.astype(np.float32)
         p, b, td, tr, rt, _ = time_form(mgr, ctx, ud, dtype, prec, n, warmup, ws, coords=coords)
+        if keep is not None:
+            keep[kname] = b[1].cpu().numpy()
         nb = ud.size * ud.itemsize
         out[name] = {"value": round(2.0 * nb / ((td + tr) * 1e-3) / 1e9, 3), "unit": UNIT,
                      "decompose_gbs": round(nb / (td * 1e-3) / 1e9, 3),
@@ -523,7 +558,7 @@ def st_section(mgr, ctx, steps, warmup):
     decompose + recompose per step, same metric as the headline."""
     import torch
 
-    from paper_2105_12764_gb300 import synth
+    synth = synth_module()
 
     shape = ST_SHAPE
     x = synth.grf_field_torch(shape, seed=5)
@@ -566,7 +601,7 @@ def st_section(mgr, ctx, steps, warmup):
     return out
 
 
-def batched_section(mgr, ctx, steps):
+def batched_section(mgr, ctx, steps, keep=None):
     """4096 independent FP32 fields of uneven 2D/3D sizes (17^2 .. 129^3 elements,
     log-uniform; half on stretched coordinates) decomposed and recomposed with
     mgr_batch_submit (one persistent launch per phase, graph replay, autotuned
@@ -574,7 +609,7 @@ def batched_section(mgr, ctx, steps):
     import numpy as np
     import torch
 
-    from paper_2105_12764_gb300 import synth
+    synth = synth_module()
 
     specs = synth.batch_field_specs(4096, seed=0)
     plans32, plans64, x32, y32, z32 = [], [], [], [], []
@@ -589,8 +624,9 @@ def batched_section(mgr, ctx, steps):
         z32.append(torch.empty_like(x32[-1]))
         elems += u.numel()
     bytes32 = elems * 4
-    dec = [(mgr.MGR_OP_DECOMPOSE, p, a, b) for p, a, b in zip(plans32, x32, y32)]
-    rec = [(mgr.MGR_OP_RECOMPOSE, p, b, c) for p, b, c in zip(plans32, y32, z32)]
+    # the request lists are marshalled once and resubmitted every step
+    dec = ctx.batch_prepare([(mgr.MGR_OP_DECOMPOSE, p, a, b) for p, a, b in zip(plans32, x32, y32)])
+    rec = ctx.batch_prepare([(mgr.MGR_OP_RECOMPOSE, p, b, c) for p, b, c in zip(plans32, y32, z32)])
 
     def step():
         ctx.batch_poll(ctx.batch_submit(dec), -1)
@@ -606,6 +642,9 @@ def batched_section(mgr, ctx, steps):
         step()
     ms = (time.perf_counter() - t0) * 1e3 / steps
     rt = max(float((c - a).abs().max() / a.abs().max()) for a, c in zip(x32[:64], z32[:64]))
+    if keep is not None:
+        keep["C4"] = [(specs[i][0], specs[i][1], x32[i].cpu().numpy(), y32[i].cpu().numpy())
+                      for i in batch_sample(specs)]
     # plain per-field FP64 path on the same fields (one graph-replayed call per field)
     x64 = [a.double() for a in x32]
     del y32, z32
@@ -644,18 +683,37 @@ def batched_section(mgr, ctx, steps):
     return out
 
 
-def serving_section(mgr, device, n_requests):
+def batch_sample(specs, k_random=40):
+    """Indices of the batch fields compared with the oracle: the 8 largest 3D and
+    2D fields, the 8 smallest, and a seeded random draw of the rest."""
+    import numpy as np
+
+    sizes = np.array([int(np.prod(s)) for s, _ in specs])
+    is3 = np.array([len(s) == 3 for s, _ in specs])
+    order = np.argsort(sizes)
+    chosen = set([int(i) for i in order[::-1] if is3[i]][:8] + [int(i) for i in order[::-1] if not is3[i]][:8] +
+                 [int(i) for i in order[:8]])
+    rest = [i for i in range(len(specs)) if i not in chosen]
+    chosen.update(int(i) for i in np.random.default_rng(2024).choice(rest, k_random, replace=False))
+    return sorted(chosen)
+
+
+def serving_section(mgr, device, n_requests, keep=None):
     """Poisson stream of requests, 70% decompose / 30% recompose of a resident
     hierarchy; cube sides log-uniform on [33, 513] (rounded to 24 log-spaced
     sizes so the client can hold one input field per size), FP32 or FP64 with
-    p = 1/2; 100 GB device-memory admission cap.  The saturated throughput is
-    measured first, then p50/p99 arrival-to-completion latency at 0.5, 0.8 and
-    0.95 of it."""
+    p = 1/2; 100 GB device-memory admission cap.  One server serves every run;
+    it is warmed first (one decomposition and recomposition per size and type,
+    outside any measured window), and each run's resident hierarchies are
+    released before the next.  The saturated throughput is measured first,
+    then arrival-to-completion latency at 0.5, 0.8 and 0.95 of it, split into
+    the wait for admission and the time on the device.  `keep` receives the
+    hierarchies of a burst of large requests (among smaller ones) for the
+    oracle comparison of the CPU-baseline leg."""
     import numpy as np
     import torch
 
-    from paper_2105_12764_gb300 import synth
-
+    synth = synth_module()
     ctx = mgr.Context(device, mem_budget_bytes=100 << 30)
     sizes = sorted(set(int(round(v)) for v in np.geomspace(33, 513, 24)))
     slots = 4
@@ -676,9 +734,19 @@ def serving_section(mgr, device, n_requests):
         return (n, dt), (mgr.MGR_OP_DECOMPOSE if rng.random() < 0.7 else mgr.MGR_OP_RECOMPOSE)
 
     reqs = [draw() for _ in range(n_requests)]
+    srv = mgr.Server(ctx, slots=slots, streams=slots)
+    # warm-up: every plan's kernels, the allocator pool and the server's streams
+    t_w = time.perf_counter()
+    for key in keys:
+        _, res = srv.wait(srv.enqueue(mgr.MGR_OP_DECOMPOSE, plans[key], inp=fields[key], keep_resident=1))
+        srv.wait(srv.enqueue(mgr.MGR_OP_RECOMPOSE, plans[key], src=res["handle"], out=outs[key][0]))
+        srv.release(res["handle"])
+    warm_s = time.perf_counter() - t_w
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
 
     def run(rate):
-        srv = mgr.Server(ctx, slots=slots, streams=slots)
         t0 = srv.now() + 0.02
         gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
         arrivals = t0 + np.cumsum(gaps)
@@ -692,7 +760,7 @@ def serving_section(mgr, device, n_requests):
                 if res is None:
                     continue
                 kind, key, slot = outstanding.pop(rid)
-                done.append(res)
+                done.append((res, kind, key))
                 if kind == mgr.MGR_OP_DECOMPOSE and res["handle"]:
                     resident.append((res["handle"], key))
                 if slot is not None:
@@ -719,43 +787,157 @@ def serving_section(mgr, device, n_requests):
             outstanding[rid] = (mgr.MGR_OP_DECOMPOSE, key, None)
             total_bytes += fields[key].numel() * fields[key].element_size()
         harvest(block=True)
-        end = max(r["done"] for r in done)
-        srv.stop()
-        lat = np.array([r["done"] - r["arrival"] for r in done]) * 1e3
-        ok = all(r["status"] == mgr.MGR_OK for r in done)
+        end = max(r["done"] for r, _, _ in done)
+        for h, _ in resident:  # the next run starts with nothing resident
+            srv.release(h)
+        lat = np.array([r["done"] - r["arrival"] for r, _, _ in done]) * 1e3
+        wait = np.array([r["admitted"] - r["arrival"] for r, _, _ in done]) * 1e3
+        serv = np.array([r["done"] - r["admitted"] for r, _, _ in done]) * 1e3
+        slow = sorted(zip(lat, done), key=lambda t: -t[0])[:5]
+        ok = all(r["status"] == mgr.MGR_OK for r, _, _ in done)
         return dict(requests=len(done), ok=ok, makespan_s=end - t0, gbs=total_bytes / (end - t0) / 1e9,
-                    req_per_s=len(done) / (end - t0), p50_ms=float(np.percentile(lat, 50)),
-                    p99_ms=float(np.percentile(lat, 99)))
+                    req_per_s=len(done) / (end - t0), p50_ms=pct(lat, 50), p99_ms=pct(lat, 99),
+                    p50_wait_ms=pct(wait, 50), p99_wait_ms=pct(wait, 99), p50_service_ms=pct(serv, 50),
+                    p99_service_ms=pct(serv, 99),
+                    slowest=[{"ms": round(float(l_), 3), "n": k[0], "dtype": "f64" if k[1] == mgr.MGR_F64 else "f32",
+                              "op": "decompose" if o == mgr.MGR_OP_DECOMPOSE else "recompose",
+                              "wait_ms": round((r["admitted"] - r["arrival"]) * 1e3, 3)}
+                             for l_, (r, o, k) in slow])
+
+    def rounded(d):
+        return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
 
     sat = run(None)
     out = {"workload": f"{n_requests} requests, 70/30 decompose/recompose, cube sides log-uniform on [33, 513] "
                        f"({len(sizes)} sizes), FP32/FP64 p=1/2, 100 GB admission cap, {slots} slots / streams",
-           "saturated": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in sat.items()}}
+           "warmup_s": round(warm_s, 3), "saturated": rounded(sat)}
     for frac in (0.5, 0.8, 0.95):
-        r = run(frac * sat["req_per_s"])
-        out[f"load_{frac}"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+        out[f"load_{frac}"] = rounded(run(frac * sat["req_per_s"]))
     out["value"] = out["saturated"]["gbs"]
     out["unit"] = "GB/s"
     out["p50_ms"] = out["load_0.8"]["p50_ms"]
     out["p99_ms"] = out["load_0.8"]["p99_ms"]
+    if keep is not None:
+        # a burst of the largest and a mid-size cube in both types, among smaller requests
+        mid = max(n for n in sizes if n <= 257)
+        targets = [(mid, mgr.MGR_F32), (mid, mgr.MGR_F64), (513, mgr.MGR_F32), (513, mgr.MGR_F64)]
+        small = [k for k in keys if k[0] <= 100]
+        order = []
+        for k, tgt in enumerate(targets):
+            order += small[3 * k: 3 * k + 3] + [tgt]
+        rids = [(key, srv.enqueue(mgr.MGR_OP_DECOMPOSE, plans[key], inp=fields[key], keep_resident=1))
+                for key in order]
+        got = {}
+        for key, rid in rids:
+            _, res = srv.wait(rid)
+            if key in targets and key not in got and res["status"] == mgr.MGR_OK:
+                h = torch.empty_like(fields[key])
+                srv.read(res["handle"], h, torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                got[key] = h.cpu().numpy()
+            if res["handle"]:
+                srv.release(res["handle"])
+        keep["C5"] = [(n, "f64" if dt == mgr.MGR_F64 else "f32", fields[(n, dt)].cpu().numpy(), got[(n, dt)])
+                      for (n, dt) in targets if (n, dt) in got]
+    srv.stop()
     for p in plans.values():
         p.close()
     ctx.close()
     return out
 
 
-def cpu_baseline(u):
+def rel_linf(a, b):
+    """Normwise relative L-infinity error max|a - b| / max|b|."""
+    import numpy as np
+
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = float(np.abs(b).max())
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def cpu_baseline(u, keep):
+    """The FP64 CPU oracle (plain C, one thread) timed on this host's cores on
+    the configurations of the workload, and, on the same seeded inputs, the
+    error (normwise relative L-inf) of the GPU results this run produced
+    against it.  FP32 forms are compared with the oracle on the FP32-rounded
+    input."""
+    import numpy as np
+
     import oracle
 
-    t = time.time()
-    c = oracle.decompose(u)
-    t_dec = time.time() - t
-    t = time.time()
-    oracle.recompose(c)
-    t_rec = time.time() - t
-    return {"value": round(2.0 * u.nbytes / (t_dec + t_rec) / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+    synth = synth_module()
+    configs, parity = {}, {}
+
+    def timed(fn):
+        t = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t
+
+    def rate(nodes, elem, seconds):
+        return {"gbs": round(nodes * elem / seconds / 1e9, 4), "mnodes_per_s": round(nodes / seconds / 1e6, 3),
+                "s": round(seconds, 3)}
+
+    # headline: 513^3 FP64, full field, decompose + recompose
+    c, t_dec = timed(lambda: oracle.decompose(u))
+    _, t_rec = timed(lambda: oracle.recompose(c))
+    head = round(2.0 * u.nbytes / (t_dec + t_rec) / 1e9, 4)
+    configs["C2 513^3 fp64"] = dict(rate(2 * u.size, 8, t_dec + t_rec), sample="full field, decompose + recompose")
+    if "C2 fp64" in keep:
+        parity["C2 513^3 fp64"] = rel_linf(keep.pop("C2 fp64"), c)
+    del c
+    if any(k in keep for k in ("C2 fp32", "C2 mixed")):
+        c32 = oracle.decompose(u.astype(np.float32).astype(np.float64))
+        for form in ("fp32", "mixed"):
+            if f"C2 {form}" in keep:
+                parity[f"C2 513^3 {form}"] = rel_linf(keep.pop(f"C2 {form}"), c32)
+        del c32
+    # 65^3 sines, FP64, decompose + recompose
+    u1, _ = synth.workload("sines65")
+    c1, t1 = timed(lambda: oracle.decompose(u1))
+    _, t1r = timed(lambda: oracle.recompose(c1))
+    configs["C1 65^3 fp64"] = dict(rate(2 * u1.size, 8, t1 + t1r), sample="full field, decompose + recompose")
+    if "C1 fp64" in keep:
+        parity["C1 65^3 fp64"] = rel_linf(keep.pop("C1 fp64"), c1)
+    # 1000x700x300 stretched: decomposition of the full field (FP64 input, then the FP32-rounded one)
+    if any(k.startswith("C3") for k in keep):
+        u3, co3 = synth.workload("bumps_stretched_1000x700x300")
+        c3, t3 = timed(lambda: oracle.decompose(u3, co3))
+        configs["C3 1000x700x300 stretched fp64"] = dict(rate(u3.size, 8, t3), sample="full field, decompose only")
+        if "C3 fp64" in keep:
+            parity["C3 1000x700x300 fp64"] = rel_linf(keep.pop("C3 fp64"), c3)
+        del c3
+        c3s = oracle.decompose(u3.astype(np.float32).astype(np.float64), co3)
+        for form in ("mixed", "fp32"):
+            if f"C3 {form}" in keep:
+                parity[f"C3 1000x700x300 {form}"] = rel_linf(keep.pop(f"C3 {form}"), c3s)
+        del c3s, u3
+    # 4096-field batch: a sample of fields, decompose + recompose, summed
+    if "C4" in keep:
+        errs, nodes, secs = [], 0, 0.0
+        for shape, st, u4, y4 in keep.pop("C4"):
+            co = [synth.stretched_coords(n) for n in shape] if st else None
+            u64 = u4.astype(np.float64)
+            c4, t4 = timed(lambda: oracle.decompose(u64, co))
+            _, t4r = timed(lambda: oracle.recompose(c4, co))
+            errs.append(rel_linf(y4, c4))
+            nodes += 2 * u64.size
+            secs += t4 + t4r
+        configs["C4 batch sample fp32 input"] = dict(rate(nodes, 4, secs),
+                                                     sample=f"{len(errs)} of the 4096 fields (largest 2D and 3D, "
+                                                            "smallest, seeded random), decompose + recompose each")
+        parity["C4 batch fp32 (worst of sample)"] = max(errs)
+        parity["C4 batch fields compared"] = len(errs)
+    # served: a burst of large requests among small ones
+    if "C5" in keep:
+        for n, dt, u5, y5 in keep.pop("C5"):
+            parity[f"C5 served {n}^3 {dt}"] = rel_linf(y5, oracle.decompose(u5.astype(np.float64)))
+    return {"value": head, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one decompose + recompose of the full {'x'.join(map(str, u.shape))} FP64 field "
-                      f"({t_dec + t_rec:.1f} s)"}
+                      f"({t_dec + t_rec:.1f} s), single thread",
+            "host": host_cores(), "threads_used": 1, "configs": configs,
+            "parity_vs_oracle": {k: (float(f"{v:.3e}") if isinstance(v, float) else v) for k, v in parity.items()},
+            "tolerances": "fp64 <= 1e-12, fp32 / mixed <= 1e-5 (normwise relative L-inf)"}
 
 
 # ------------------------------------------------------- reference arm -----
@@ -788,7 +970,8 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded k^-5/3 GRF",
            "config": {"workload": f"{'x'.join(map(str, shape))} uniform grid, FP64, full hierarchy, decompose + "
                                   "recompose per step (CPU oracle on a bounded sample)", "shape": list(shape)},
-           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": host_cores(), "threads_used": 1},
            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -102,6 +102,29 @@ int mgr_shutdown(mgr_ctx* ctx);
 int mgr_max_levels(const mgr_desc* desc, int* levels);
 int mgr_default_levels(const mgr_desc* desc, int* levels);
 
+/* The FP64 tables a plan for `desc` would hold for one axis at one level,
+   built on the host only (no context, no device, nothing allocated on a GPU):
+   the inspection point of the operators of Sec. II.A / III.A.
+     level     1..L of the resolved depth (desc->levels = -1: the default)
+     axis      0..ndim-1 in the order of desc->shape (ndim-1 fastest; axis 0
+               of a 4D field is time)
+     n, m      out: nodes of this axis at level `level` and at level-1
+     wa, wb    n entries: interpolation weights of each fine node on its left
+               and right coarse neighbours (Sec. II.A.1); 0 at coarse nodes
+     k         5*m entries: row q holds the mass-transfer taps K = P^T M
+               (Sec. III.A.2) at fine nodes min(2q, n-1)-2 .. +2, scaled by
+               1/u_q, u_q the pivots of the coarse mass matrix's LU factors
+               (Sec. III.A.3); taps outside 0..n-1 are 0
+     ta, tb    m entries: the scaled Thomas recurrences, forward
+               y_q = f'_q - ta_q y_{q-1}, backward z_q = y_q - tb_q z_{q+1}
+     cap       capacity of each of wa, wb, k, ta, tb in doubles
+   With all five arrays NULL only n and m are returned.  MGR_EINVAL for an
+   invalid description, level or axis, or when cap < max(n, 5*m) with any
+   array given.  An axis that does not coarsen at this level reports
+   n = m = 1 and the identity stencil. */
+int mgr_plan_tables_host(const mgr_desc* desc, int level, int axis, int* n, int* m, double* wa, double* wb,
+                         double* k, double* ta, double* tb, int cap);
+
 /* Build a plan: the hierarchy, every interpolation weight, the mass-transfer
    stencils K = P^T M (Sec. III.A.2, formed as P^T M in FP64 from the
    coordinates) and the factors of the coarse mass matrices for the Thomas
@@ -253,10 +276,14 @@ int mgr_recompose_dequantized(const mgr_plan* plan, const int32_t* codes, int nc
    launches the kernels directly on `stream`.
      - Returns MGR_EINVAL when the plan's mgr_workspace_size() exceeds
        MGR_NOALLOC_SCRATCH_BYTES (for example FP64 fields of more than about
-       15 million nodes), and for the argument errors of mgr_decompose.
-     - The first call on a device looks up the area's device address (with
-       that device made current for the lookup); make that first call before
-       any stream capture.
+       15 million nodes), and for the argument errors of mgr_decompose
+       (among them in == out for a 4D plan, which runs out of place only).
+     - The plan's device must be the calling thread's current device (the
+       kernels use that device's copy of the area); MGR_EINVAL otherwise.
+     - The first call on a device looks up the area's device address; make
+       that first call before any stream capture.  A first call made while
+       `stream` is being captured returns MGR_EINVAL and leaves the capture
+       untouched.
      - Every call on a device shares the one area, which keeps the previous
        call's contents (nothing in it needs to start at zero).  Calls whose
        work overlaps on the GPU (different streams, or other host threads)

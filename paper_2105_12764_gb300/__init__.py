@@ -17,6 +17,7 @@ __all__ = [
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
     "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE",
     "MGR_OP_DECOMPOSE_PACKED", "MGR_OP_RECOMPOSE_PACKED", "Server", "lib", "library_path", "Context", "Plan", "EXPORTED",
+    "PreparedBatch", "plan_tables_host",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -102,6 +103,10 @@ EXPORTED = {
     "mgr_shutdown": (_i, [_vp]),
     "mgr_max_levels": (_i, [ctypes.POINTER(mgr_desc), ctypes.POINTER(_i)]),
     "mgr_default_levels": (_i, [ctypes.POINTER(mgr_desc), ctypes.POINTER(_i)]),
+    "mgr_plan_tables_host": (_i, [ctypes.POINTER(mgr_desc), _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), _i]),
     "mgr_plan_create": (_i, [_vp, ctypes.POINTER(mgr_desc), ctypes.POINTER(_vp)]),
     "mgr_plan_destroy": (_i, [_vp]),
     "mgr_plan_levels": (_i, [_vp, ctypes.POINTER(_i)]),
@@ -203,6 +208,26 @@ def make_desc(shape, coords=None, levels=-1, dtype=MGR_F64, prec=MGR_PREC_NATIVE
     return d, keep
 
 
+def plan_tables_host(shape, coords=None, levels=-1, level=1, axis=0, dtype=MGR_F64, prec=MGR_PREC_NATIVE):
+    """mgr_plan_tables_host: the FP64 tables of one axis at one level, built on the
+    host (no device).  Returns dict(n, m, wa, wb, k (m x 5), ta, tb) of numpy arrays."""
+    import numpy as np
+
+    d, keep = make_desc(shape, coords, levels, dtype, prec)
+    n, m = _i(), _i()
+    _check("mgr_plan_tables_host", lib.mgr_plan_tables_host(ctypes.byref(d), int(level), int(axis), ctypes.byref(n),
+                                                             ctypes.byref(m), None, None, None, None, None, 0))
+    cap = max(n.value, 5 * m.value)
+    bufs = [np.zeros(cap) for _ in range(5)]
+    dp = [b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for b in bufs]
+    _check("mgr_plan_tables_host", lib.mgr_plan_tables_host(ctypes.byref(d), int(level), int(axis), ctypes.byref(n),
+                                                             ctypes.byref(m), *dp, cap))
+    del keep
+    nn, mm = n.value, m.value
+    return dict(n=nn, m=mm, wa=bufs[0][:nn].copy(), wb=bufs[1][:nn].copy(), k=bufs[2][:5 * mm].reshape(mm, 5).copy(),
+                ta=bufs[3][:mm].copy(), tb=bufs[4][:mm].copy())
+
+
 class Context:
     """mgr_init / mgr_shutdown."""
 
@@ -223,20 +248,20 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
+    @staticmethod
+    def batch_prepare(requests):
+        """The mgr_request array of a request list, marshalled once: a list that is
+        submitted again and again (every step of a loop) can be passed to
+        batch_submit as this object, without re-marshalling thousands of entries
+        per call.  Holds references to the plans and tensors it names."""
+        return PreparedBatch(requests)
+
     def batch_submit(self, requests):
-        """mgr_batch_submit; requests: iterable of (op, plan, in, out[, user_tag]).  Returns the ticket."""
-        reqs = list(requests)
-        arr = (mgr_request * max(1, len(reqs)))()
-        for i, r in enumerate(reqs):
-            op, plan, src, dst = r[:4]
-            arr[i].op = int(op)
-            arr[i].plan = plan.handle
-            arr[i].in_ = _ptr(src)
-            arr[i].out = _ptr(dst)
-            arr[i].user_tag = int(r[4]) if len(r) > 4 else i
-            arr[i].keep_resident = 0
+        """mgr_batch_submit; requests: iterable of (op, plan, in, out[, user_tag]), or a
+        PreparedBatch (batch_prepare).  Returns the ticket."""
+        pb = requests if isinstance(requests, PreparedBatch) else PreparedBatch(requests)
         t = ctypes.c_uint64()
-        _check("mgr_batch_submit", lib.mgr_batch_submit(self.handle, arr, len(reqs), ctypes.byref(t)))
+        _check("mgr_batch_submit", lib.mgr_batch_submit(self.handle, pb.arr, pb.n, ctypes.byref(t)))
         return t.value
 
     def batch_poll(self, ticket, timeout_us=-1):
@@ -251,6 +276,24 @@ class Context:
         buf = ctypes.create_string_buffer(1 << 16)
         lib.mgr_batch_tuning(self.handle, buf, len(buf))
         return buf.value.decode()
+
+
+class PreparedBatch:
+    """A marshalled mgr_request array (see Context.batch_prepare)."""
+
+    def __init__(self, requests):
+        reqs = list(requests)
+        self.n = len(reqs)
+        self.arr = (mgr_request * max(1, self.n))()
+        self._refs = reqs  # the plans and buffers must outlive the array's use
+        for i, r in enumerate(reqs):
+            op, plan, src, dst = r[:4]
+            self.arr[i].op = int(op)
+            self.arr[i].plan = plan.handle
+            self.arr[i].in_ = _ptr(src)
+            self.arr[i].out = _ptr(dst)
+            self.arr[i].user_tag = int(r[4]) if len(r) > 4 else i
+            self.arr[i].keep_resident = 0
 
 
 class Plan:

@@ -6,12 +6,28 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 
 #include "mgr_internal.h"
 
 namespace mgr {
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limits;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limits[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 bool fault_injected(const char* what) {
   const char* v = std::getenv("MGR_FAULT_INJECT");
@@ -335,6 +351,44 @@ int mgr_max_levels(const mgr_desc* desc, int* levels) {
 int mgr_default_levels(const mgr_desc* desc, int* levels) {
   if (!levels) return MGR_EINVAL;
   return mgr::resolve_levels(desc, nullptr, nullptr, levels);
+}
+
+int mgr_plan_tables_host(const mgr_desc* desc, int level, int axis, int* n, int* m, double* wa, double* wb,
+                         double* k, double* ta, double* tb, int cap) {
+  if (!desc || !n || !m) return MGR_EINVAL;
+  int L = 0;
+  int rc = mgr::resolve_levels(desc, &L, nullptr, nullptr);
+  if (rc != MGR_OK) return rc;
+  if (level < 1 || level > L || axis < 0 || axis >= desc->ndim) return MGR_EINVAL;
+  mgr_plan p;
+  p.desc = *desc;
+  for (int a = desc->ndim; a < 4; ++a) {
+    p.desc.shape[a] = 0;
+    p.desc.coords[a] = nullptr;
+  }
+  p.levels = L;
+  try {
+    rc = mgr::build_plan_tables(&p);
+  } catch (const std::bad_alloc&) {
+    return MGR_ENOMEM;
+  }
+  if (rc != MGR_OK) return rc;
+  // desc axis -> internal axis: 4D puts time apart; fewer than three spatial
+  // dimensions are the fastest internal axes
+  const bool st = desc->ndim == 4;
+  const int lead = mgr::kAxes - (st ? 3 : desc->ndim);
+  const mgr::AxisLevel& ax = (st && axis == 0) ? p.geom[level].tax : p.geom[level].ax[(st ? axis - 1 : axis) + lead];
+  *n = ax.n;
+  *m = ax.m;
+  if (!wa && !wb && !k && !ta && !tb) return MGR_OK;
+  if (cap < std::max(ax.n, 5 * ax.m)) return MGR_EINVAL;
+  const double* T = p.tables.host.data();
+  if (wa) std::copy(T + ax.o_wa, T + ax.o_wa + ax.n, wa);
+  if (wb) std::copy(T + ax.o_wb, T + ax.o_wb + ax.n, wb);
+  if (k) std::copy(T + ax.o_k, T + ax.o_k + 5 * ax.m, k);
+  if (ta) std::copy(T + ax.o_ta, T + ax.o_ta + ax.m, ta);
+  if (tb) std::copy(T + ax.o_tb, T + ax.o_tb + ax.m, tb);
+  return MGR_OK;
 }
 
 int mgr_plan_create(mgr_ctx* ctx, const mgr_desc* desc, mgr_plan** plan) {

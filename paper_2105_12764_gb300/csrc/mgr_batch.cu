@@ -561,9 +561,13 @@ struct BatchExec {
     if (dev) cudaFree(dev);
   }
   cudaError_t enqueue(cudaStream_t st) const {
+    static const char* kinds[] = {"level pass", "interpolation", "strided solves", "contiguous solves",
+                                  "coarsest copy"};
+    NvtxRange op_range("mgr batch: %d phases", int(launches.size()));
     for (auto& c : copies) c(st);
     for (const L& l : launches) {
-      if (l.smem > 48 * 1024) cudaFuncSetAttribute(l.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(l.smem));
+      NvtxRange phase_range("batch phase: %s", kinds[l.kind]);
+      raise_smem_limit(l.fn, l.smem);
       if (l.kind == 4) {
         void* args[] = {const_cast<void**>(&l.desc), const_cast<int*>(&l.n)};
         cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
@@ -631,7 +635,7 @@ struct BatchState {
   std::map<uint64_t, Ticket> tickets;
   // executable batches keyed by the request list
   struct Entry {
-    std::string key;
+    std::vector<const void*> key;  // op, then (plan, in, out) of every request
     void* ws = nullptr;
     size_t ws_bytes = 0;
     std::unique_ptr<BatchExec> exec;
@@ -718,23 +722,26 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
 
 template <typename TD, typename TS, typename TW>
 int run_group(mgr_ctx* ctx, BatchState& B, const std::vector<const mgr_request*>& reqs, int op) {
-  // workspace / executable lookup keyed by the exact request list
-  std::string key = std::to_string(op) + "|";
-  std::vector<const mgr_plan*> plans;
+  // workspace / executable lookup keyed by the exact request list (a vector of
+  // pointers: a resubmitted list is found with one comparison per entry)
+  std::vector<const void*> key;
+  key.reserve(1 + 3 * reqs.size());
+  key.push_back(reinterpret_cast<const void*>(uintptr_t(op)));
   size_t ws_total = 0;
   for (const mgr_request* r : reqs) {
-    char buf[80];
-    std::snprintf(buf, sizeof(buf), "%p:%p:%p;", (const void*)r->plan, r->in, r->out);
-    key += buf;
-    plans.push_back(r->plan);
+    key.push_back(r->plan);
+    key.push_back(r->in);
+    key.push_back(r->out);
     ws_total += (r->plan->ws_bytes + 255) & ~size_t(255);
   }
-  const int form = reqs[0]->plan->form;
-  const std::string skey = shape_key(plans, op, form);
   BatchState::Entry* ent = nullptr;
   for (auto& e : B.entries)
     if (e->key == key) ent = e.get();
   if (!ent) {
+    std::vector<const mgr_plan*> plans;
+    plans.reserve(reqs.size());
+    for (const mgr_request* r : reqs) plans.push_back(r->plan);
+    const std::string skey = shape_key(plans, op, reqs[0]->plan->form);
     if (ctx->budget && ws_total > ctx->budget) return MGR_EBUDGET;
     // evict least recently used entries until the new workspace fits the budget
     while (ctx->budget && B.held_bytes + ws_total > ctx->budget && !B.entries.empty()) {
@@ -746,7 +753,7 @@ int run_group(mgr_ctx* ctx, BatchState& B, const std::vector<const mgr_request*>
       B.entries.erase(victim);
     }
     auto e = std::make_unique<BatchState::Entry>();
-    e->key = key;
+    e->key = std::move(key);
     e->ws_bytes = std::max<size_t>(ws_total, 256);
     if (fault_injected("alloc")) return MGR_ENOMEM;
     if (cudaMalloc(&e->ws, e->ws_bytes) != cudaSuccess) {

@@ -96,7 +96,7 @@ cudaError_t launch_small(const mgr_plan* p, SmallArgs<TS, TW>& a, cudaStream_t s
   const int ls = a.levels;
   const size_t sm = small_smem_bytes<TS, TW>(a.n[ls][0], a.n[ls][1], a.n[ls][2], a.m[ls][0], a.m[ls][1], a.m[ls][2]);
   auto kern = DEC ? k_small_dec<TD, TS, TW> : k_small_rec<TD, TS, TW>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   rec_begin(st);
   kern<<<1, kSmallThreads, sm, st>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -205,7 +205,9 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   TW* F = static_cast<TW*>(b.F);
   TW* cur = nullptr;  // compact level-l values for l < L
   const int ls = (PK || QZ) ? 0 : small_levels<TS, TW>(p);  // levels ls..1 run in one CTA
+  NvtxRange op_range("mgr decompose %s", PK ? (QZ ? "quantized" : "packed") : "nodal");
   for (int l = L; l > ls; --l) {
+    NvtxRange level_range("decompose level %d", l);
     TW* nxt = static_cast<TW*>(((L - l) % 2 == 0) ? b.A : b.B);
     auto a = level_args<TS, TW>(p, l);
     const LevelGeom& g = p->geom[l];
@@ -269,6 +271,7 @@ cudaError_t decompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     cur = nxt;
   }
   if (ls >= 1) {
+    NvtxRange small_range("decompose levels %d..1 in one CTA", ls);
     SmallArgs<TS, TW> sa = small_args<TS, TW>(p, ls);
     sa.vin = ls == L ? in : static_cast<const void*>(cur);
     sa.vin_full = ls == L;
@@ -325,6 +328,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   auto Fl = [&](int l) { return reinterpret_cast<TW*>(static_cast<char*>(b.F) + p->f_off[l]); };
   // load vector of level l (Sec. II.A.2) from its coefficients, on stream s
   auto load_vector = [&](int l, cudaStream_t s) -> cudaError_t {
+    NvtxRange lv_range("recompose level %d load vector", l);
     const LevelGeom& g = p->geom[l];
     auto a = level_args<TS, TW>(p, l);
     a.in = PK ? static_cast<const void*>(static_cast<const TY*>(in) + p->class_off[l]) : in;
@@ -359,6 +363,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
   const int last_lv = std::min(L, ncls - 1);  // levels 1..last_lv have their coefficient class
   const int ls = (PK || QZ) ? 0 : small_levels<TS, TW>(p);  // levels 1..ls run in one CTA
   const bool fork = fk != nullptr && last_lv > ls && t_recorder == nullptr;
+  NvtxRange op_range("mgr recompose %s", PK ? (QZ ? "dequantized" : "packed") : "nodal");
   if (rp && cudaStreamWaitEvent(st, rp->even, 0) != cudaSuccess) return cudaGetLastError();
   if (fork) {
     if (cudaEventRecord(fk->ev[0], st) != cudaSuccess || cudaStreamWaitEvent(fk->side, fk->ev[0], 0) != cudaSuccess)
@@ -398,6 +403,7 @@ cudaError_t recompose_t(const mgr_plan* p, const void* in, void* out, void* ws, 
     if (e != cudaSuccess) return e;
   }
   for (int l = ls + 1; l <= L; ++l) {
+    NvtxRange level_range("recompose level %d", l);
     const LevelGeom& g = p->geom[l];
     const void* cl = PK ? static_cast<const void*>(static_cast<const TY*>(in) + p->class_off[l]) : in;
     const double qs = QZ ? bins[l] : 1.0;

@@ -8,8 +8,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <cstdarg>
+#include <cstdio>
 #include <cstddef>
 #include <cstdint>
 #include <mutex>
@@ -143,12 +146,42 @@ Work work_level_load(const mgr_plan* p, int l, bool decompose);
 Work work_solve(const mgr_plan* p, int l, int axis, bool final_op);
 Work work_interp(const mgr_plan* p, int l);
 
+// NVTX range over host-side enqueue work: one per operation and one per
+// level, so a profiler's timeline groups the launches of each level.  A CUDA
+// graph replay runs no host code, so its launches fall under the ranges of
+// the capture that built the graph.  Costs a few nanoseconds when no
+// profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* fmt, ...) {
+    char buf[64];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Host-side fault injection for tests (no GPU fault is involved): true when
 // the comma-separated list in the environment variable MGR_FAULT_INJECT
 // names `what` ("alloc": device allocations of the batch / serving layers
 // fail; "launch": operations fail before any kernel is launched; "admit":
 // serving admission refuses requests).  Read on every call.
 bool fault_injected(const char* what);
+
+// Raise the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes`.  The limit only ever grows: a launch captured into a
+// graph (or issued from another thread) with a larger request than the
+// current one is never left above a lowered limit.  Requests up to the 48 KB
+// that every kernel may use without the attribute need no call.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+template <typename F>
+inline cudaError_t raise_smem_limit(F* fn, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(fn), bytes);
+}
 
 // mgr_plan.cpp
 int build_plan_tables(mgr_plan* p);

@@ -114,7 +114,7 @@ void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
   using C = LevelCfg<TS>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   dim3 grid = level_grid(p, a);
   kern<<<grid, C::NW * 32, sm, st>>>(a);
 }
@@ -127,7 +127,7 @@ void launch_level_chunks(const mgr_plan* p, LevelArgs<TS, TW>& a, int c0, int c1
   using C = LevelCfg<TS>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   dim3 grid = level_grid(p, a);
   if (c1 <= c0 || c1 > int(grid.z)) return;
   a.bz0 = c0;
@@ -196,7 +196,7 @@ void launch_interp_chunks(const mgr_plan* p, int l, const void* c, const TW* w, 
   a.bz0 = c0;
   constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
   auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK, QZ>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   kern<<<dim3(gx, gy, c1 - c0), kInterpNW * 32, sm, st>>>(a);
 }
 
@@ -234,7 +234,7 @@ cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t line
   R = std::max(1, R);
   const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
   const int blocks = int((lines + R - 1) / R);
-  cudaFuncSetAttribute(k_solve_contig<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(k_solve_contig<TW>, sm);
   k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines, mx, R, ta, tb, op);
   return cudaGetLastError();
 }
@@ -272,7 +272,7 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   const size_t ssm = solve_staged_smem<TW>(mline);
   if (lines < 32768 && ssm <= size_t(100) * 1024 && ssm <= p->ctx->smem_optin) {
     // few lines (coarse levels): whole lines staged in shared memory, 32 per CTA
-    cudaFuncSetAttribute(k_solve_staged<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ssm));
+    raise_smem_limit(k_solve_staged<TW>, ssm);
     k_solve_staged<TW><<<int((lines + kStagedLines - 1) / kStagedLines), 128, ssm, st>>>(f, w, mline, lstride, inner,
                                                                                        outer, ostride, ta, tb, op);
     return cudaGetLastError();

@@ -33,23 +33,22 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on `device`, looked up on first use.
-int scratch_address(int device, void** out) {
+// Device address of the scratch array on `device`, looked up on first use
+// (with `device` current: the caller checked that it is).  A first use while
+// `stream` is being captured is refused: the lookup may load the library's
+// device image, which a capture does not allow.
+int scratch_address(int device, cudaStream_t stream, void** out) {
   if (device < 0 || device >= kMaxDevices) return MGR_EINVAL;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_ptr[device]) {
-    int cur = -1;
-    if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
       cudaGetLastError();
       return MGR_ECUDA;
     }
-    if (cur != device && cudaSetDevice(device) != cudaSuccess) {
-      cudaGetLastError();
-      return MGR_ECUDA;
-    }
+    if (cap != cudaStreamCaptureStatusNone) return MGR_EINVAL;
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (cur != device) cudaSetDevice(cur);
     if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
       return MGR_ECUDA;
@@ -74,15 +73,27 @@ extern "C" int mgr_decompose_noalloc(const mgr_plan* plan, const void* in, void*
   const size_t bytes = size_t(plan->count) * plan->elem;
   if ((reinterpret_cast<uintptr_t>(in) % plan->elem) || (reinterpret_cast<uintptr_t>(out) % plan->elem))
     return MGR_EINVAL;
-  if (in != out && overlap(in, bytes, out, bytes)) return MGR_EINVAL;
+  // in place only where mgr_decompose allows it: never for 4D plans, whose
+  // time passes read neighbouring slices after their coefficients are written
+  const bool alias_ok = plan->desc.ndim != 4;
+  if ((in != out || !alias_ok) && overlap(in, bytes, out, bytes)) return MGR_EINVAL;
+  // the kernels run on the current device and use that device's copy of the
+  // scratch array: it must be the plan's device
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ECUDA;
+  }
+  if (cur != plan->ctx->device) return MGR_EINVAL;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   void* ws = nullptr;
-  const int rc = scratch_address(plan->ctx->device, &ws);
+  const int rc = scratch_address(cur, st, &ws);
   if (rc != MGR_OK) return rc;
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return MGR_ECUDA;
   }
-  const cudaError_t e = mgr::enqueue_decompose(plan, in, out, ws, reinterpret_cast<cudaStream_t>(stream));
+  const cudaError_t e = mgr::enqueue_decompose(plan, in, out, ws, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return MGR_ECUDA;

@@ -221,7 +221,7 @@ cudaError_t launch_level_st(const mgr_plan* p, LevelArgs<TS, TW>& a, Slabs sl, i
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   sl.zchunks = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   auto kern = k_level_st<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   kern<<<dim3(gx, gy, sl.zchunks * slabs), C::NW * 32, sm, st>>>(a, sl);
   return cudaGetLastError();
 }
@@ -237,7 +237,7 @@ cudaError_t launch_interp_st(const mgr_plan* p, int l, const TD* c, const TW* w,
   sl.zchunks = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
   auto kern = k_interp_st<kInterpNW, kInterpRPW, TD, TO, TS, TW>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  raise_smem_limit(kern, sm);
   kern<<<dim3(gx, gy, sl.zchunks * slabs), kInterpNW * 32, sm, st>>>(a, sl);
   return cudaGetLastError();
 }
@@ -345,7 +345,9 @@ cudaError_t decompose_st_t(const mgr_plan* p, const void* in, void* out, void* w
   TD* y = static_cast<TD*>(out);
   const int64_t Fsp = space_full_count(p);
   TW* cur = nullptr;
+  NvtxRange op_range("mgr decompose 4D");
   for (int l = L; l >= 1; --l) {
+    NvtxRange level_range("decompose 4D level %d", l);
     const LevelGeom& g = p->geom[l];
     const int nt = g.tax.n, mt = g.tax.m;
     const int64_t Sn = g.space_fine(), Sm = g.space_coarse();
@@ -441,7 +443,9 @@ cudaError_t recompose_st_t(const mgr_plan* p, const void* in, void* out, void* w
   TW* cur = static_cast<TW*>((L % 2 == 1) ? b.A : b.B);
   cudaError_t e = coarsest_st<TD, TW>(p, c, cur, 0, st);
   if (e != cudaSuccess) return e;
+  NvtxRange op_range("mgr recompose 4D");
   for (int l = 1; l <= L; ++l) {
+    NvtxRange level_range("recompose 4D level %d", l);
     const LevelGeom& g = p->geom[l];
     const int nt = g.tax.n, mt = g.tax.m;
     const int64_t Sn = g.space_fine(), Sm = g.space_coarse();

@@ -7,6 +7,15 @@ CUDA-event time and the achieved bandwidth / flop rate of its algorithmic
 work (mgr_profile), then the graph-replayed decompose and recompose times.
 With --plain it only runs the operations (no event brackets): a clean target
 for an external profiler.
+
+    python -m paper_2105_12764_gb300.profile --batch 4096 [--form fp32] [--reps 1]
+
+submits the batched workload (the given number of uneven 2D / 3D fields,
+element counts log-uniform on [17^2, 129^3], half on stretched coordinates)
+once to autotune and capture it, then times `reps` decompose + recompose
+submits; only those submits run between cudaProfilerStart and
+cudaProfilerStop (an external profiler started with profiling off captures
+exactly their launches).
 """
 import argparse
 import os
@@ -26,7 +35,10 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--plain", action="store_true")
     ap.add_argument("--packed", action="store_true", help="class-packed decompose / recompose")
+    ap.add_argument("--batch", type=int, default=0, help="batched workload of this many fields")
     a = ap.parse_args()
+    if a.batch:
+        return batch_main(a)
     shape = tuple(int(v) for v in a.shape.split(","))
     if len(shape) == 1:
         shape = shape * 3
@@ -85,6 +97,52 @@ def main():
     print(f"graph-replayed: decompose {ev[0].elapsed_time(ev[1]) / a.reps:.3f} ms, "
           f"recompose {ev[1].elapsed_time(ev[2]) / a.reps:.3f} ms")
     plan.close()
+    ctx.close()
+
+
+def batch_main(a):
+    import time
+
+    import torch
+
+    import paper_2105_12764_gb300 as mgr
+    from paper_2105_12764_gb300 import synth
+
+    dtype = mgr.MGR_F64 if a.form == "fp64" else mgr.MGR_F32
+    prec = mgr.MGR_PREC_MIXED if a.form == "mixed" else mgr.MGR_PREC_NATIVE
+    ctx = mgr.Context(0)
+    specs = synth.batch_field_specs(a.batch, seed=0)
+    plans, xs, ys, zs = [], [], [], []
+    for i, (shape, st) in enumerate(specs):
+        coords = [synth.stretched_coords(n) for n in shape] if st else None
+        plans.append(mgr.Plan(ctx, shape, coords, -1, dtype, prec))
+        u = synth.grf_field_torch(shape, seed=1000 + i)
+        xs.append(u if dtype == mgr.MGR_F64 else u.float())
+        ys.append(torch.empty_like(xs[-1]))
+        zs.append(torch.empty_like(xs[-1]))
+    dec = ctx.batch_prepare([(mgr.MGR_OP_DECOMPOSE, p, x, y) for p, x, y in zip(plans, xs, ys)])
+    rec = ctx.batch_prepare([(mgr.MGR_OP_RECOMPOSE, p, y, z) for p, y, z in zip(plans, ys, zs)])
+
+    def step():
+        ctx.batch_poll(ctx.batch_submit(dec), -1)
+        ctx.batch_poll(ctx.batch_submit(rec), -1)
+
+    step()  # autotune + graph capture
+    step()
+    torch.cuda.synchronize()
+    cudart = torch.cuda.cudart()
+    cudart.cudaProfilerStart()
+    t0 = time.perf_counter()
+    for _ in range(a.reps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / a.reps
+    cudart.cudaProfilerStop()
+    elems = sum(x.numel() for x in xs)
+    print(f"batch of {len(specs)} fields ({a.form}), {elems} elements: {ms:.3f} ms per decompose + recompose "
+          f"submit pair; {ctx.batch_tuning().strip()[:300]}")
+    for p in plans:
+        p.close()
     ctx.close()
 
 

@@ -86,3 +86,48 @@ def test_traffic_only_for_unchanged_sources(tmp_path, monkeypatch):
 def test_single_rank_helpers():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     bench.barrier(1)
+
+
+def test_reference_arm_does_not_load_the_cuda_library():
+    """The reference (CPU oracle) arm imports the input generators by path, so
+    neither the package nor libmgr.so enters its process."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys, json; sys.argv = ['bench.py', '--impl', 'reference', '--shape', '17,18,19', "
+            "'--steps', '1', '--warmup', '0']; import bench; bench.main(); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'libmgr.so' not in maps, 'libmgr.so mapped'; "
+            "assert 'paper_2105_12764_gb300' not in sys.modules, 'package imported'")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["cpu_baseline"]["threads_used"] == 1
+    assert line["cpu_baseline"]["host"]["host_cores"] >= 1
+
+
+def test_batch_sample_covers_extremes_and_both_coordinate_kinds():
+    import numpy as np
+
+    synth = bench.synth_module()
+    specs = synth.batch_field_specs(4096, seed=0)
+    idx = bench.batch_sample(specs)
+    assert len(idx) == 64 and len(set(idx)) == 64
+    sizes = [int(np.prod(s)) for s, _ in specs]
+    assert max(sizes) in [sizes[i] for i in idx]
+    assert min(sizes) in [sizes[i] for i in idx]
+    assert {len(specs[i][0]) for i in idx} == {2, 3}
+    assert {specs[i][1] for i in idx} == {False, True}
+    assert idx == bench.batch_sample(specs)  # seeded
+
+
+def test_rel_linf_is_normwise():
+    import numpy as np
+
+    b = np.array([1.0, -4.0, 0.0])
+    a = np.array([1.0, -4.0, 1e-3])
+    assert bench.rel_linf(a, b) == 1e-3 / 4.0
+    assert bench.rel_linf(np.zeros(3), np.zeros(3)) == 0.0
