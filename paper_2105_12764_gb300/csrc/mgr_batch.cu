@@ -44,6 +44,7 @@ namespace {
 #include "mgr_device.cuh"
 #include "mgr_level.cuh"
 #include "mgr_solve.cuh"
+#include "mgr_small.cuh"
 
 // ---------------------------------------------------------------------------
 // Descriptor-driven kernels (one CTA per work item, persistent grid)
@@ -58,7 +59,7 @@ __device__ __forceinline__ void copy_words(T* dst, const T* src) {
 }
 
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) kb_level(const LevelArgs<TS, TW>* __restrict__ args,
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_level(const LevelArgs<TS, TW>* __restrict__ args,
                                                        const int4* __restrict__ items, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) LevelArgs<TS, TW> sa;
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(NW * 32, 2) kb_level(const LevelArgs<TS, TW>* 
 }
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) kb_interp(const InterpArgs<TS, TW>* __restrict__ args,
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_interp(const InterpArgs<TS, TW>* __restrict__ args,
                                                         const int4* __restrict__ items, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) InterpArgs<TS, TW> sa;
@@ -115,6 +116,24 @@ __global__ void __launch_bounds__(128) kb_solve_contig(const SolveDesc<TW>* __re
     const SolveDesc<TW> s = d[it.x];
     solve_contig_rows<TW>(s.f, s.w, s.mline, s.count, s.row_pitch, s.R, s.ta, s.tb, s.op, int64_t(it.y) * s.R,
                           smem_raw);
+    __syncthreads();
+  }
+}
+
+// The coarse end of every field's hierarchy (its levels of at most a few
+// thousand nodes), one field per CTA: the one-CTA coarse-level bodies of the
+// single-field path, over a list of fields (largest first).
+constexpr int kBatchSmallThreads = 512;
+
+template <bool DEC, typename TD, typename TS, typename TW>
+__global__ void __launch_bounds__(kBatchSmallThreads, 2) kb_small(const SmallArgs<TS, TW>* __restrict__ args, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) SmallArgs<TS, TW> sa;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    copy_words(&sa, args + i);
+    __syncthreads();
+    if (DEC) small_dec_body<TD, TS, TW>(sa, smem_raw);
+    else small_rec_body<TD, TS, TW>(sa, smem_raw);
     __syncthreads();
   }
 }
@@ -185,7 +204,7 @@ struct Builder {
   Blob blob;
   struct PendingPhase {
     const void* fn;
-    int kind;            // 0 level, 1 interp, 2 strided, 3 contig, 4 coarsest
+    int kind;            // 0 level, 1 interp, 2 strided, 3 contig, 4 coarsest, 5 coarse levels in one CTA
     size_t desc_off, items_off;
     int n_items;
     int block;
@@ -195,7 +214,31 @@ struct Builder {
   std::vector<PendingPhase> pending;
   std::vector<std::function<void(cudaStream_t)>> copies;  // levels == 0 fields
 
-  Builder(const std::vector<FieldRef>& f, int o, TileCand c, int sms) : fields(f), op(o), cand(c), num_sms(sms) {}
+  std::vector<int> small;  // per field: its levels 1..small[f] run in one CTA (kb_small)
+  size_t smem_optin;
+
+  Builder(const std::vector<FieldRef>& f, int o, TileCand c, int sms, size_t optin)
+      : fields(f), op(o), cand(c), num_sms(sms), smem_optin(optin) {
+    for (const FieldRef& fr : fields) small.push_back(small_levels_of(fr.p));
+  }
+
+  // Coarse levels taken by the one-CTA phase: the largest ls whose level grid
+  // has at most 8192 nodes and whose work arrays fit in kSmallSmemCap bytes
+  // (two CTAs per SM).
+  static constexpr size_t kSmallSmemCap = size_t(100) * 1024;
+  int small_levels_of(const mgr_plan* p) const {
+    int ls = 0;
+    for (int l = 1; l <= p->levels && l <= kSmallMaxLevels; ++l) {
+      const LevelGeom& g = p->geom[l];
+      const size_t sm =
+          small_smem_bytes<TS, TW>(g.ax[0].n, g.ax[1].n, g.ax[2].n, g.ax[0].m, g.ax[1].m, g.ax[2].m);
+      if (g.space_fine() > 8192 || sm > kSmallSmemCap || sm > smem_optin) break;
+      ls = l;
+    }
+    return ls;
+  }
+  // whether field i runs level L - d in the tiled phases
+  bool tiled(size_t i, int d) const { return fields[i].p->levels - d > small[i]; }
 
   static char* bufA(const FieldRef& fr) { return fr.ws; }
   static char* bufB(const FieldRef& fr) { return fr.ws + fr.p->ws_a; }
@@ -229,9 +272,10 @@ struct Builder {
     std::vector<LevelArgs<TS, TW>> descs;
     std::vector<int4> items;
     const int BX = 30, BY = cfg_by(cand.cfg);
-    for (const FieldRef& fr : fields) {
+    for (size_t fi = 0; fi < fields.size(); ++fi) {
+      const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
-      if (L <= d) continue;
+      if (!tiled(fi, d)) continue;
       const int l = L - d;
       LevelArgs<TS, TW> a = level_args(fr, l);
       if (MODE == 0) {
@@ -297,9 +341,10 @@ struct Builder {
     std::vector<InterpArgs<TS, TW>> descs;
     std::vector<int4> items;
     constexpr int NW = 8, RPW = 2, BY = NW * RPW;
-    for (const FieldRef& fr : fields) {
+    for (size_t fi = 0; fi < fields.size(); ++fi) {
+      const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
-      if (L <= d) continue;
+      if (!tiled(fi, d)) continue;
       const int l = L - d;
       const mgr_plan* p = fr.p;
       const LevelGeom& g = p->geom[l];
@@ -354,9 +399,10 @@ struct Builder {
     std::vector<SolveDesc<TW>> sdesc, cdesc;
     std::vector<int2> sitems, citems;
     size_t csmem = 0;
-    for (const FieldRef& fr : fields) {
+    for (size_t fi = 0; fi < fields.size(); ++fi) {
+      const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
-      if (L <= d) continue;
+      if (!tiled(fi, d)) continue;
       const int l = L - d;
       const LevelGeom& g = fr.p->geom[l];
       if (!g.ax[axis].active) continue;
@@ -427,10 +473,11 @@ struct Builder {
 
   void coarsest_phase(int dir) {
     std::vector<CopyDesc<TD, TW>> descs;
-    for (const FieldRef& fr : fields) {
+    for (size_t fi = 0; fi < fields.size(); ++fi) {
+      const FieldRef& fr = fields[fi];
       const mgr_plan* p = fr.p;
       const int L = p->levels;
-      if (L == 0) continue;
+      if (L == 0 || small[fi] > 0) continue;  // the one-CTA phase handles the coarsest grid
       CopyDesc<TD, TW> c{};
       c.y = static_cast<TD*>(dir == 1 ? fr.out : const_cast<void*>(fr.in));
       // level-0 values: where the last decomposition level wrote them / where
@@ -458,6 +505,76 @@ struct Builder {
     pending.push_back(ph);
   }
 
+  // The one-CTA phase: every field's levels small[f]..1 (decomposition: after
+  // its tiled levels; recomposition: before them), largest first.
+  void small_phase(bool dec) {
+    std::vector<std::pair<size_t, size_t>> order;  // (shared memory, field)
+    for (size_t fi = 0; fi < fields.size(); ++fi) {
+      const int ls = small[fi];
+      if (ls < 1) continue;
+      const LevelGeom& g = fields[fi].p->geom[ls];
+      order.push_back({small_smem_bytes<TS, TW>(g.ax[0].n, g.ax[1].n, g.ax[2].n, g.ax[0].m, g.ax[1].m, g.ax[2].m), fi});
+    }
+    if (order.empty()) return;
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<SmallArgs<TS, TW>> descs;
+    for (const auto& o : order) {
+      const FieldRef& fr = fields[o.second];
+      const mgr_plan* p = fr.p;
+      const int L = p->levels, ls = small[o.second];
+      SmallArgs<TS, TW> a{};
+      const TS* T = table_of<TS>(p);
+      const TW* Tw = table_of<TW>(p);
+      a.levels = ls;
+      for (int l = 1; l <= ls; ++l)
+        for (int k = 0; k < 3; ++k) {
+          const AxisLevel& ax = p->geom[l].ax[k];
+          a.n[l][k] = ax.n;
+          a.m[l][k] = ax.m;
+          a.active[l][k] = ax.active ? 1 : 0;
+          a.s[l][k] = ax.s;
+          a.wa[l][k] = T + ax.o_wa;
+          a.wb[l][k] = T + ax.o_wb;
+          a.k[l][k] = T + ax.o_k;
+          a.ta[l][k] = Tw + ax.o_ta;
+          a.tb[l][k] = Tw + ax.o_tb;
+        }
+      const int64_t s0 = int64_t(1) << L;
+      for (int k = 0; k < 3; ++k) {
+        a.N[k] = p->full[k];
+        a.n0[k] = int(p->coarsest[k]);
+        a.s0[k] = p->full[k] > 1 ? s0 : 1;
+      }
+      a.sz = p->full[1] * p->full[2];
+      a.sy = p->full[2];
+      // level-ls values: the field itself when every level is small, else the
+      // coarse buffer the tiled level ls+1 writes (decomposition) / the
+      // interpolation of level ls+1 reads (recomposition)
+      char* lsbuf = ((L - ls - 1) % 2 == 0) ? bufA(fr) : bufB(fr);
+      if (dec) {
+        a.vin = ls == L ? fr.in : static_cast<const void*>(lsbuf);
+        a.vin_full = ls == L;
+        a.out = fr.out;
+      } else {
+        a.cin = fr.in;
+        a.vout = ls == L ? fr.out : static_cast<void*>(lsbuf);
+        a.vout_full = ls == L;
+      }
+      descs.push_back(a);
+    }
+    PendingPhase ph{};
+    ph.kind = 5;
+    ph.desc_off = blob.put(descs.data(), descs.size() * sizeof(descs[0]));
+    ph.items_off = 0;
+    ph.n_items = int(descs.size());
+    ph.fn = dec ? reinterpret_cast<const void*>(kb_small<true, TD, TS, TW>)
+                : reinterpret_cast<const void*>(kb_small<false, TD, TS, TW>);
+    ph.block = kBatchSmallThreads;
+    ph.smem = order.front().first;
+    ph.grid = std::min(ph.n_items, num_sms * 2);
+    pending.push_back(ph);
+  }
+
   void build() {
     int D = 0;
     for (const FieldRef& fr : fields) D = std::max(D, fr.p->levels);
@@ -477,9 +594,11 @@ struct Builder {
         solve_phase(d, 1, SOLVE_ADD);
         solve_phase(d, 0, SOLVE_ADD);
       }
+      small_phase(true);
       coarsest_phase(1);
     } else {
       coarsest_phase(0);
+      small_phase(false);
       for (int d = D - 1; d >= 0; --d) {
         level_phase<1, TD>(d, false);
         solve_phase(d, 2, SOLVE_SUB);
@@ -506,9 +625,10 @@ struct Builder {
     for (int d = 0; d < D; ++d) {
       std::vector<double> jobs;
       double bytes = 0;
-      for (const FieldRef& fr : fields) {
+      for (size_t fi = 0; fi < fields.size(); ++fi) {
+        const FieldRef& fr = fields[fi];
         const int L = fr.p->levels;
-        if (L <= d) continue;
+        if (!tiled(fi, d)) continue;
         const LevelGeom& g = fr.p->geom[L - d];
         const int chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
         const int gx = (g.ax[2].m + 29) / 30, gy = (g.ax[1].m + BY - 1) / BY;
@@ -562,13 +682,13 @@ struct BatchExec {
   }
   cudaError_t enqueue(cudaStream_t st) const {
     static const char* kinds[] = {"level pass", "interpolation", "strided solves", "contiguous solves",
-                                  "coarsest copy"};
+                                  "coarsest copy", "coarse levels in one CTA"};
     NvtxRange op_range("mgr batch: %d phases", int(launches.size()));
     for (auto& c : copies) c(st);
     for (const L& l : launches) {
       NvtxRange phase_range("batch phase: %s", kinds[l.kind]);
       raise_smem_limit(l.fn, l.smem);
-      if (l.kind == 4) {
+      if (l.kind == 4 || l.kind == 5) {
         void* args[] = {const_cast<void**>(&l.desc), const_cast<int*>(&l.n)};
         cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
         if (e != cudaSuccess) return e;
@@ -583,8 +703,9 @@ struct BatchExec {
 };
 
 template <typename TD, typename TS, typename TW>
-int make_exec(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms, std::unique_ptr<BatchExec>& out) {
-  Builder<TD, TS, TW> b(fields, op, cand, num_sms);
+int make_exec(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms, size_t optin,
+              std::unique_ptr<BatchExec>& out) {
+  Builder<TD, TS, TW> b(fields, op, cand, num_sms, optin);
   b.build();
   auto ex = std::make_unique<BatchExec>();
   ex->dev_bytes = std::max<size_t>(b.blob.host.size(), 16);
@@ -614,8 +735,8 @@ int make_exec(const std::vector<FieldRef>& fields, int op, TileCand cand, int nu
 }
 
 template <typename TD, typename TS, typename TW>
-double model_of(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms) {
-  Builder<TD, TS, TW> b(fields, op, cand, num_sms);
+double model_of(const std::vector<FieldRef>& fields, int op, TileCand cand, int num_sms, size_t optin) {
+  Builder<TD, TS, TW> b(fields, op, cand, num_sms, optin);
   return b.model_cost(6.79e6 * 0.6);  // bytes per microsecond at ~60% of the measured copy bandwidth
 }
 
@@ -670,14 +791,14 @@ int exec_for(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fields, i
              TileCand cand, std::unique_ptr<BatchExec>& out) {
   (void)B;
   (void)skey;
-  return make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, out);
+  return make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ctx->smem_optin, out);
 }
 
 // Time one candidate on the real batch (graph-less, after one warm-up run).
 template <typename TD, typename TS, typename TW>
 double time_candidate(mgr_ctx* ctx, const std::vector<FieldRef>& fields, int op, TileCand cand, cudaStream_t st) {
   std::unique_ptr<BatchExec> ex;
-  if (make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ex) != MGR_OK) return 1e30;
+  if (make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ctx->smem_optin, ex) != MGR_OK) return 1e30;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -701,7 +822,7 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
   for (int cfg = 0; cfg < kNumCfg; ++cfg)
     for (int chunk : {8, 16, 32}) {
       TileCand c{cfg, chunk};
-      ranked.push_back({model_of<TD, TS, TW>(fields, op, c, ctx->num_sms), c});
+      ranked.push_back({model_of<TD, TS, TW>(fields, op, c, ctx->num_sms, ctx->smem_optin), c});
     }
   std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
   TileCand best = ranked[0].second;

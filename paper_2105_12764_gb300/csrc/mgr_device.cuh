@@ -27,6 +27,19 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+// The same copy of `bytes` (4, 8 or 16) that reads nothing and writes zeros
+// when `valid` is false (the copy's source-size operand): a branch-free
+// predicated load.  `gmem` must be a valid address either way.
+__device__ __forceinline__ void cp_async_zf(void* smem, const void* gmem, int bytes, bool valid) {
+  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const unsigned n = valid ? unsigned(bytes) : 0u;
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {

@@ -103,7 +103,7 @@ dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
   using C = LevelCfg<TS>;
   using G = LevelTile<C::NW, C::RPW>;
   const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
+  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], level_ctas_per_sm(C::NW));
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   return dim3(gx, gy, gz);

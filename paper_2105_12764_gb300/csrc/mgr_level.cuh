@@ -26,7 +26,7 @@
 // shared memory, the x stencil runs on rows (5 taps; 2 on rows that are
 // coarse in y and z, where c vanishes on coarse nodes), the y stencil on
 // the x results, and the z stencil accumulates in registers over the
-// streamed planes.  Four barriers per plane pair.
+// streamed planes.  Three barriers per plane pair (FP32) or four (FP64).
 //
 // Coefficient addressing.  Nodal (PK = false): a coefficient sits at its node's
 // full-grid position.  Class-packed (PK = true, Sec. I coefficient classes): the
@@ -56,17 +56,44 @@ struct LevelTile {
 // Tile configuration of the level pass per stencil type: 8 warps with two
 // row pairs each (two CTAs per SM); FP64 uses a single cp.async stage (the
 // FP64 pipe, not memory latency, bounds it, and the smaller footprint keeps
-// two CTAs per SM), FP32 two stages.
+// two CTAs per SM), FP32 two stages.  The MGR_LEVEL_* macros override the
+// defaults at build time (tuning sweeps).
+#ifndef MGR_LEVEL_F64_NW
+#define MGR_LEVEL_F64_NW 8
+#endif
+#ifndef MGR_LEVEL_F64_RPW
+#define MGR_LEVEL_F64_RPW 2
+#endif
+#ifndef MGR_LEVEL_F64_STAGES
+#define MGR_LEVEL_F64_STAGES 1
+#endif
+#ifndef MGR_LEVEL_F32_NW
+#define MGR_LEVEL_F32_NW 8
+#endif
+#ifndef MGR_LEVEL_F32_RPW
+#define MGR_LEVEL_F32_RPW 2
+#endif
+#ifndef MGR_LEVEL_F32_STAGES
+#define MGR_LEVEL_F32_STAGES 2
+#endif
 template <typename TS>
 struct LevelCfg;
 template <>
 struct LevelCfg<double> {
-  static constexpr int NW = 8, RPW = 2, STAGES = 1;
+  static constexpr int NW = MGR_LEVEL_F64_NW, RPW = MGR_LEVEL_F64_RPW, STAGES = MGR_LEVEL_F64_STAGES;
 };
 template <>
 struct LevelCfg<float> {
-  static constexpr int NW = 8, RPW = 2, STAGES = 2;
+  static constexpr int NW = MGR_LEVEL_F32_NW, RPW = MGR_LEVEL_F32_RPW, STAGES = MGR_LEVEL_F32_STAGES;
 };
+
+// CTAs per SM a level-pass or interpolation CTA of NW warps is compiled for:
+// 16 warps per SM in every configuration, so each thread may use up to 128
+// registers.
+#ifndef MGR_LEVEL_CTAS_16W
+#define MGR_LEVEL_CTAS_16W 1
+#endif
+constexpr int level_ctas_per_sm(int nw) { return nw >= 16 ? MGR_LEVEL_CTAS_16W : 16 / nw; }
 template <typename T>
 struct Pair;
 template <>
@@ -180,7 +207,7 @@ template <int NW, int RPW, int STAGES, typename TI, typename TS>
 constexpr size_t level_smem_bytes() {
   using G = LevelTile<NW, RPW>;
   return sizeof(TI) * STAGES * 2 * G::RR * G::RC +
-         sizeof(TS) * (2 * G::RR * G::CP + NW * G::RC + 2 * G::RR * 32 + 5 * 32 + 5 * NW * RPW);
+         sizeof(TS) * (2 * G::RR * G::CP + 2 * G::RR * 32 + 5 * 32 + 5 * NW * RPW + (sizeof(TS) == 8 ? NW * G::RC : 0));
 }
 
 // Copy the element pair (c0, c0+1) of one row into shared memory: one
@@ -237,10 +264,10 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   constexpr unsigned FULL = 0xffffffffu;
   TI* stage = reinterpret_cast<TI*>(smem_raw);                                       // [STAGES][2][RR][RC]
   TS* cbuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * STAGES * 2 * RR * RC);  // [2][RR][CP]
-  TS* xch = cbuf + 2 * RR * CP;                                                     // [NW][RC]
-  TS* gxb = xch + NW * RC;                                                          // [2][RR][32]
+  TS* gxb = cbuf + 2 * RR * CP;                                                     // [2][RR][32]
   TS* kxs = gxb + 2 * RR * 32;                                                      // [5][32]
   TS* kys = kxs + 5 * 32;                                                           // [5][NW*RPW]
+  TS* xch = kys + 5 * NW * RPW;  // [NW][RC] FP64 only: x interpolants of each warp's first coarse row
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
@@ -286,8 +313,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const bool fx1 = vx1 && gx1 < nx - 1;  // gx1 is odd: fine unless it is the last node
   const TS wax1 = fx1 ? a.wa[2][gx1] : TS(0), wbx1 = fx1 ? a.wb[2][gx1] : TS(0);
   const bool owx0 = vx0 && gx0 >= ox0 && gx0 < ox1, owx1 = vx1 && gx1 >= ox0 && gx1 < ox1;
-  const int ic0 = a.in_full ? int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])) : gx0;
-  const int ic1 = a.in_full ? int(fmap(min(gx1, nx - 1), a.s[2], a.N[2])) : gx1;
+  // input columns, clamped into the grid (slots past its end load zeros from a valid address)
+  const int ic0 = a.in_full ? int(fmap(min(gx0, nx - 1), a.s[2], a.N[2])) : min(gx0, nx - 1);
+  const int ic1 = a.in_full ? int(fmap(min(gx1, nx - 1), a.s[2], a.N[2])) : min(gx1, nx - 1);
   const int yc0 = PK ? gx0 : int(fmap(min(gx0, nx - 1), a.s[2], a.N[2]));
   const int yc1 = PK ? gx1 : int(fmap(min(gx1, nx - 1), a.s[2], a.N[2]));
   const bool ycontig = yc1 == yc0 + 1;
@@ -318,6 +346,23 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   };
   // interior column: taps px +- 1 fine, px and px +- 2 coarse, even slot
   const bool kx_generic = kxm == 31u && (px & 1) == 0 && px + 1 < nx - 1;
+  // FP32 (BF): the x / y stencils run without per-row branches, always five
+  // taps (weight 0 outside the grid) over tiles whose slots outside the region
+  // hold zeros, so their 8 independent FMA chains per thread interleave (the
+  // FP32 pass is latency-bound); FP64, bound by its FP64 pipe, keeps the
+  // reduced tap counts of rows whose coefficients vanish.
+  constexpr bool BF = sizeof(TS) == 4;
+  // FP32 nodal decomposition (RS): the coefficients go out after the
+  // coefficient phase, row by row from the shared tile, each lane storing
+  // output columns ox0 + lane and ox0 + 32 + lane (consecutive lanes,
+  // consecutive addresses): the coefficient phase then keeps no output
+  // addresses or values live (it is short of registers).  All-coarse nodes
+  // get 0 there, a placeholder a coarser level overwrites.
+  constexpr bool RS = BF && !PK && MODE == 0;
+  const int oc0 = ox0 + lane, oc1 = oc0 + 32;
+  const bool rs0 = oc0 < ox1, rs1 = oc1 < ox1;
+  const int ro0 = int(fmap(min(oc0, nx - 1), a.s[2], a.N[2])), ro1 = int(fmap(min(oc1, nx - 1), a.s[2], a.N[2]));
+  const int rsl0 = oc0 - rx0, rsl1 = oc1 - rx0;
 
   // ---- per-row constants (RPW row pairs per warp)
   int gy0[RPW];
@@ -391,19 +436,33 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         }
         continue;
       }
-      if (vy0[k]) {
-        if (vx0) cp_async(d0, base + ir0[k] + ic0, int(sizeof(TI)));
-        if (vx1) cp_async(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)));
-      }
-      if (vy1[k]) {
-        if (vx0) cp_async(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)));
-        if (vx1) cp_async(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)));
+      if constexpr (MODE == 1) {
+        // branch-free: every slot is copied, slots outside the region as zeros
+        // (their addresses are clamped into the grid, so they are valid)
+        cp_async_zf(d0, base + ir0[k] + ic0, int(sizeof(TI)), vy0[k] && vx0);
+        cp_async_zf(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)), vy0[k] && vx1);
+        cp_async_zf(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)), vy1[k] && vx0);
+        cp_async_zf(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)), vy1[k] && vx1);
+      } else {
+        // (the decomposition pass is short of registers: copying only the slots
+        // inside the region keeps its per-slot predicates out of the loop)
+        if (vy0[k]) {
+          if (vx0) cp_async(d0, base + ir0[k] + ic0, int(sizeof(TI)));
+          if (vx1) cp_async(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)));
+        }
+        if (vy1[k]) {
+          if (vx0) cp_async(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)));
+          if (vx1) cp_async(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)));
+        }
       }
     }
   };
   auto has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
+  static_assert(STAGES == 1 || STAGES == 2, "one or two stage buffers");
+  // stage buffer of plane pair t (two in rotation, or one)
+  auto stage_of = [&](int t) { return stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0); };
   auto issue = [&](int t) {
-    TI* sb = stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0);
+    TI* sb = stage_of(t);
     load_plane(sb, pidx(t, nz), true);
     if (has_fine(t)) load_plane(sb + RR * RC, pidx(t, nz) - 1, false);
     cp_commit();
@@ -418,11 +477,13 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     for (int e = 0; e < 4; ++e) Ip[k][e] = In[k][e] = TS(0);
   }
 
+  // two stages: the next plane pair is in flight while this one is processed;
+  // one stage: the next is issued once every thread is done with the stage
   issue(t_start);
   for (int t = t_start; t <= t_end; ++t) {
     if (STAGES == 2) {
       if (t < t_end) {
-        issue(t + 1);
+        issue(t + 1);  // into the buffer plane pair t-1 used
         cp_wait<1>();
       } else {
         cp_wait<0>();
@@ -431,7 +492,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       cp_wait<0>();
     }
     __syncthreads();
-    const TI* sc = stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0);
+    const TI* sc = stage_of(t);
     const TI* sf = sc + RR * RC;
     const int Pc = pidx(t, nz);
     const bool hf = has_fine(t);
@@ -465,8 +526,22 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         In[k][1] = fx1 ? wax1 * vc[k][0] + wbx1 * v02 : vc[k][1];
       }
     }
-    if (MODE == 0) *reinterpret_cast<TS2*>(xch + warp * RC + cx0) = TS2{In[0][0], In[0][1]};
-    __syncthreads();
+    // the x interpolant of the coarse row below this warp's last pair (the next
+    // warp's first row), for the y interpolation of this warp's last fine row.
+    // FP32: computed here from the staged tile (the same operations as the next
+    // warp's), so no exchange and no barrier is needed; FP64, bound by its FP64
+    // pipe, takes it from the next warp through shared memory instead.
+    TS nxt0 = TS(0), nxt1 = TS(0);
+    if constexpr (!BF) {
+      if (MODE == 0) *reinterpret_cast<TS2*>(xch + warp * RC + cx0) = TS2{In[0][0], In[0][1]};
+      __syncthreads();
+    } else if (MODE == 0 && warp + 1 < NW) {
+      const TI2 pn = *reinterpret_cast<const TI2*>(sc + 2 * (warp + 1) * RPW * RC + cx0);
+      const TS vn0 = cval(pn.x), vn1 = cval(pn.y);
+      const TS vn2 = __shfl_down_sync(FULL, vn0, 1);
+      nxt0 = vn0;
+      nxt1 = fx1 ? wax1 * vn0 + wbx1 * vn2 : vn1;
+    }
 
     // ---- coefficients of both planes -> shared memory and the nodal output
     TS* cc = cbuf;
@@ -484,9 +559,14 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           n0 = In[k + 1 < RPW ? k + 1 : k][0];
           n1 = In[k + 1 < RPW ? k + 1 : k][1];
         } else if (warp + 1 < NW) {
-          const TS2 nx2 = *reinterpret_cast<const TS2*>(xch + (warp + 1) * RC + cx0);
-          n0 = nx2.x;
-          n1 = nx2.y;
+          if constexpr (BF) {
+            n0 = nxt0;
+            n1 = nxt1;
+          } else {
+            const TS2 nx2 = *reinterpret_cast<const TS2*>(xch + (warp + 1) * RC + cx0);
+            n0 = nx2.x;
+            n1 = nx2.y;
+          }
         } else {
           n0 = n1 = TS(0);
         }
@@ -512,6 +592,14 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         c[2] = fy1[k] ? vc[k][2] : TS(0);
         c[3] = (fx1 || fy1[k]) ? vc[k][3] : TS(0);
       }
+      if constexpr (BF && (PK || MODE == 0)) {
+        // slots outside the region hold zeros, not values of unloaded slots (the
+        // nodal recomposition loads zero-fill them; the other loads skip them)
+        c[0] = (vx0 && vy0[k]) ? c[0] : TS(0);
+        c[1] = (vx1 && vy0[k]) ? c[1] : TS(0);
+        c[2] = (vx0 && vy1[k]) ? c[2] : TS(0);
+        c[3] = (vx1 && vy1[k]) ? c[3] : TS(0);
+      }
       *reinterpret_cast<TS2*>(cc + r0 * CP + cx0) = TS2{c[0], c[1]};
       *reinterpret_cast<TS2*>(cc + (r0 + 1) * CP + cx0) = TS2{c[2], c[3]};
       if (PK && wy && own_c) {
@@ -525,7 +613,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
             yzc[r1 + pcx1] = yval(c[3], true);
           }
         }
-      } else if (wy && own_c) {
+      } else if (!RS && wy && own_c) {
         // all-coarse nodes get their (uncorrected) value as a placeholder that a
         // coarser level overwrites; it keeps the row's sectors fully written
         store_pair<TD>(yzc + yr0[k] + yc0, yzc + yr0[k] + yc1, TD(vc[k][0]), TD(fx1 ? c[1] : vc[k][1]),
@@ -562,22 +650,92 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 #pragma unroll
           for (int e = 0; e < 4; ++e) d[e] = vf[e];
         }
+        if constexpr (BF && (PK || MODE == 0)) {
+          d[0] = (vx0 && vy0[k]) ? d[0] : TS(0);
+          d[1] = (vx1 && vy0[k]) ? d[1] : TS(0);
+          d[2] = (vx0 && vy1[k]) ? d[2] : TS(0);
+          d[3] = (vx1 && vy1[k]) ? d[3] : TS(0);
+        }
         *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
         *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
-        if (wy && own_f) {
+        if (!RS && wy && own_f) {
           store_pair<TD>(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, yval(d[0], owy0[k] && owx0), yval(d[1], owy0[k] && owx1), owy0[k] && owx0,
                          owy0[k] && owx1, ycontig);
           store_pair<TD>(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, yval(d[2], owy1[k] && owx0), yval(d[3], owy1[k] && owx1), owy1[k] && owx0,
                          owy1[k] && owx1, ycontig);
         }
+      } else if constexpr (BF) {
+        // no fine plane: its stencils run on zeros
+        *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{TS(0), TS(0)};
+        *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{TS(0), TS(0)};
       }
     }
     __syncthreads();
 
     if (STAGES == 1 && t < t_end) issue(t + 1);  // every thread is done with the stage buffer
 
+    // ---- coefficients of this warp's owned rows (RS), from the shared tile
+    if constexpr (RS) {
+      if (wy && (own_c || own_f)) {
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = 2 * (warp * RPW + k) + h;
+            const bool orow = h == 0 ? owy0[k] : owy1[k];
+            const int yr = h == 0 ? yr0[k] : yr1[k];
+            if (orow && own_c) {
+              if (rs0) yzc[yr + ro0] = TD(cc[r * CP + rsl0]);
+              if (rs1) yzc[yr + ro1] = TD(cc[r * CP + rsl1]);
+            }
+            if (orow && own_f) {
+              if (rs0) yzf[yr + ro0] = TD(cf[r * CP + rsl0]);
+              if (rs1) yzf[yr + ro1] = TD(cf[r * CP + rsl1]);
+            }
+          }
+        }
+      }
+    }
+
     // ---- x stencil on every row of this warp (both planes)
-    if (kxo) {
+    if (BF && kxo && kx_generic) {
+      // every row's five taps from (aligned pair, pair, single) loads, both planes
+#pragma unroll
+      for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = 2 * (warp * RPW + k) + h;
+          const TS* row = cc + r * CP + dx - 2;
+          const TS* rf = cf + r * CP + dx - 2;
+          const TS2 a01 = *reinterpret_cast<const TS2*>(row);
+          const TS2 a23 = *reinterpret_cast<const TS2*>(row + 2);
+          const TS2 b01 = *reinterpret_cast<const TS2*>(rf);
+          const TS2 b23 = *reinterpret_cast<const TS2*>(rf + 2);
+          gxb[r * 32 + lane] = kx(0) * a01.x + kx(1) * a01.y + kx(2) * a23.x + kx(3) * a23.y + kx(4) * row[4];
+          gxb[RR * 32 + r * 32 + lane] = kx(0) * b01.x + kx(1) * b01.y + kx(2) * b23.x + kx(3) * b23.y + kx(4) * rf[4];
+        }
+      }
+    } else if (BF && kxo) {
+      // boundary columns: clamped slots, weight 0 outside the grid
+#pragma unroll
+      for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = 2 * (warp * RPW + k) + h;
+          const TS* row = cc + r * CP;
+          const TS* rf = cf + r * CP;
+          TS g = TS(0), gf = TS(0);
+#pragma unroll
+          for (int o = 0; o < 5; ++o) {
+            const int j = min(max(dx - 2 + o, 0), RC - 1);  // weight 0 where clamped
+            g += kx(o) * row[j];
+            gf += kx(o) * rf[j];
+          }
+          gxb[r * 32 + lane] = g;
+          gxb[RR * 32 + r * 32 + lane] = gf;
+        }
+      }
+    } else if (!BF && kxo) {
 #pragma unroll
       for (int k = 0; k < RPW; ++k) {
 #pragma unroll
@@ -635,7 +793,32 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int j = warp * RPW + k;
-      if (j < nby && kxo) {
+      if constexpr (BF) {
+        // both planes, five taps each; rows clamped into the tile (weight 0 where clamped);
+        // computed on every lane, stored only where the output exists
+        const TS* gcol = gxb + lane;
+        TS gc = TS(0), gf = TS(0);
+        if (kym[k] == 31u) {
+          const TS* g0 = gcol + (dyo[k] - 2) * 32;
+          gc = ky(k, 0) * g0[0] + ky(k, 1) * g0[32] + ky(k, 2) * g0[64] + ky(k, 3) * g0[96] + ky(k, 4) * g0[128];
+          const TS* f0 = g0 + RR * 32;
+          gf = ky(k, 0) * f0[0] + ky(k, 1) * f0[32] + ky(k, 2) * f0[64] + ky(k, 3) * f0[96] + ky(k, 4) * f0[128];
+        } else {
+#pragma unroll
+          for (int o = 0; o < 5; ++o) {
+            const int rr = min(max(dyo[k] + o - 2, 0), RR - 1);
+            gc += ky(k, o) * gcol[rr * 32];
+            gf += ky(k, o) * gcol[RR * 32 + rr * 32];
+          }
+        }
+        acc0[k] += wzc[0] * gc;
+        acc1[k] += wzc[1] * gc;
+        acc2[k] += wzc[2] * gc;
+        acc0[k] += wzf[0] * gf;
+        acc1[k] += wzf[1] * gf;
+        if (j < nby && kxo && t - 1 >= qz0 && t - 1 < qz1)
+          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
+      } else if (j < nby && kxo) {
         TS gc = TS(0), gf = TS(0);
         const TS* gcol = gxb + (dyo[k] - 2) * 32 + lane;
         if (kym[k] == 31u) {  // interior row: all five taps inside the grid
@@ -682,7 +865,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 }
 
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ>
-__global__ void __launch_bounds__(NW * 32, 2) k_level(const LevelArgs<TS, TW> a) {
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_level(const LevelArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0, smem_raw);
 }
@@ -912,7 +1095,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
 }
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
-__global__ void __launch_bounds__(NW * 32, 2) k_interp(const InterpArgs<TS, TW> a) {
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_interp(const InterpArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   interp_body<NW, RPW, TD, TO, TS, TW, PK, QZ>(a, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0, smem_raw);
 }

@@ -167,9 +167,10 @@ __device__ __forceinline__ void small_solves(TW* f, const int* m, const int* act
   }
 }
 
+// One field's coarse levels, decomposition: the body of k_small_dec and of
+// the batched one-CTA phase (smem_raw: small_smem_bytes of level a.levels).
 template <typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(kSmallThreads, 1) k_small_dec(const SmallArgs<TS, TW> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsigned char* smem_raw) {
   const int ls = a.levels;
   const int64_t nv = int64_t(a.n[ls][0]) * a.n[ls][1] * a.n[ls][2];
   const int64_t mv = int64_t(a.m[ls][0]) * a.m[ls][1] * a.m[ls][2];
@@ -229,8 +230,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_dec(const SmallArgs<
 }
 
 template <typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(kSmallThreads, 1) k_small_rec(const SmallArgs<TS, TW> a) {
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_dec(const SmallArgs<TS, TW> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  small_dec_body<TD, TS, TW>(a, smem_raw);
+}
+
+// One field's coarse levels, recomposition (see small_dec_body).
+template <typename TD, typename TS, typename TW>
+__device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsigned char* smem_raw) {
   const int ls = a.levels;
   const int64_t nv = int64_t(a.n[ls][0]) * a.n[ls][1] * a.n[ls][2];
   const int64_t mv = int64_t(a.m[ls][0]) * a.m[ls][1] * a.m[ls][2];
@@ -289,4 +296,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_rec(const SmallArgs<
       static_cast<TW*>(a.vout)[e] = V[e];
     }
   }
+}
+
+template <typename TD, typename TS, typename TW>
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_rec(const SmallArgs<TS, TW> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  small_rec_body<TD, TS, TW>(a, smem_raw);
 }

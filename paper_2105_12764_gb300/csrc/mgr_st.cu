@@ -71,7 +71,7 @@ __device__ __forceinline__ int64_t slab_map(const Slabs& sl, int t, int full) {
 }
 
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) k_level_st(const LevelArgs<TS, TW> a, const Slabs sl) {
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_level_st(const LevelArgs<TS, TW> a, const Slabs sl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.z / sl.zchunks, bz = blockIdx.z - j * sl.zchunks;
   const int t = slab_time(sl, j);
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_level_st(const LevelArgs<TS, TW>
 }
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
-__global__ void __launch_bounds__(NW * 32, 2) k_interp_st(const InterpArgs<TS, TW> a, const Slabs sl) {
+__global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_interp_st(const InterpArgs<TS, TW> a, const Slabs sl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = blockIdx.z / sl.zchunks, bz = blockIdx.z - j * sl.zchunks;
   const int t = slab_time(sl, j);
@@ -217,7 +217,7 @@ cudaError_t launch_level_st(const mgr_plan* p, LevelArgs<TS, TW>& a, Slabs sl, i
   using G = LevelTile<C::NW, C::RPW>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], 2);
+  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], level_ctas_per_sm(C::NW));
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   sl.zchunks = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   auto kern = k_level_st<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>;
