@@ -14,13 +14,15 @@
 // stream order inside the graph, so no CTA ever waits on another.
 //
 // Autotuning (Sec. III.B: an analytic model ranks the candidate launch
-// shapes, the top three are measured): candidates are the level-pass tile
+// shapes, the best few are measured): candidates are the level-pass tile
 // (8 warps x 2 row pairs = 30x14 coarse nodes, or 4 warps x 2 = 30x6) and the
-// z-chunk length (8, 16 or 32 coarse planes).  The model charges each work
-// item the shared-memory slots it streams (halo and padding included) and
-// takes the longer of the memory time and the longest-processing-time
-// schedule of the items over the persistent CTAs; the three best are timed
-// on the real batch and the fastest is cached per batch shape.
+// z-chunk length (at most 8, 16 or 32 coarse planes, split evenly over a
+// field's items).  The model charges each work item the shared-memory slots
+// it streams (halo and padding included) and takes the longer of the memory
+// time and the longest-processing-time schedule of the items over the
+// persistent CTAs; the model's best candidate of each tile shape, and the
+// next best up to three, are timed on the real batch and the fastest is
+// cached per batch shape.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -195,6 +197,14 @@ inline int cfg_by(int cfg) { return cfg == 0 ? 14 : 6; }
 
 inline int ctas_per_sm(int cfg) { return cfg == 0 ? 2 : 4; }
 
+// Coarse z planes per work item: at most `chunk`, split evenly over the items
+// (33 planes in chunks of 32 are 17 + 16, not 32 + 1).
+inline int balanced_chunk(int chunk, int mz) {
+  mz = std::max(1, mz);
+  const int items = (mz + chunk - 1) / chunk;
+  return (mz + items - 1) / items;
+}
+
 template <typename TD, typename TS, typename TW>
 struct Builder {
   const std::vector<FieldRef>& fields;
@@ -262,7 +272,7 @@ struct Builder {
     a.y_sy = p->full[2];
     a.c_sz = int64_t(g.ax[1].m) * g.ax[2].m;
     a.c_sy = g.ax[2].m;
-    a.qz_chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+    a.qz_chunk = balanced_chunk(cand.chunk, g.ax[0].m);
     return a;
   }
 
@@ -372,7 +382,7 @@ struct Builder {
       a.out_full = last ? 1 : 0;
       a.o_sz = last ? a.y_sz : int64_t(g.ax[1].n) * g.ax[2].n;
       a.o_sy = last ? a.y_sy : int64_t(g.ax[2].n);
-      a.qz_chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+      a.qz_chunk = balanced_chunk(cand.chunk, g.ax[0].m);
       const int di = int(descs.size());
       descs.push_back(a);
       const int gx = (a.m[2] + 31) / 32, gy = (a.m[1] + BY - 1) / BY, gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
@@ -630,7 +640,7 @@ struct Builder {
         const int L = fr.p->levels;
         if (!tiled(fi, d)) continue;
         const LevelGeom& g = fr.p->geom[L - d];
-        const int chunk = std::min(cand.chunk, std::max(1, g.ax[0].m));
+        const int chunk = balanced_chunk(cand.chunk, g.ax[0].m);
         const int gx = (g.ax[2].m + 29) / 30, gy = (g.ax[1].m + BY - 1) / BY;
         const int gz = (g.ax[0].m + chunk - 1) / chunk;
         for (int z = 0; z < gz; ++z) {
@@ -825,15 +835,31 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
       ranked.push_back({model_of<TD, TS, TW>(fields, op, c, ctx->num_sms, ctx->smem_optin), c});
     }
   std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  // measured: the model's best candidate of every tile shape, then the next
+  // best overall up to three (the model ranks chunk lengths well, tile
+  // shapes less so)
+  std::vector<TileCand> timed;
+  for (int cfg = 0; cfg < kNumCfg; ++cfg)
+    for (const auto& r : ranked)
+      if (r.second.cfg == cfg) {
+        timed.push_back(r.second);
+        break;
+      }
+  for (const auto& r : ranked) {
+    if (timed.size() >= 3) break;
+    bool seen = false;
+    for (const TileCand& c : timed) seen |= c.cfg == r.second.cfg && c.chunk == r.second.chunk;
+    if (!seen) timed.push_back(r.second);
+  }
   TileCand best = ranked[0].second;
   double best_ms = 1e30;
   std::vector<std::pair<TileCand, double>> log;
-  for (int i = 0; i < 3 && i < int(ranked.size()); ++i) {
-    const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, ranked[i].second, B.stream);
-    log.push_back({ranked[i].second, ms});
+  for (const TileCand& c : timed) {
+    const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, c, B.stream);
+    log.push_back({c, ms});
     if (ms < best_ms) {
       best_ms = ms;
-      best = ranked[i].second;
+      best = c;
     }
   }
   B.tuned[skey] = best;

@@ -96,19 +96,19 @@ size_t solve_staged_smem(int mline) {
   return sizeof(TW) * (size_t(mline) * kStagedLines + 2 * size_t(mline)) + sizeof(int64_t) * kStagedLines;
 }
 
+// Lines l0 .. l0+31 of the axis (the body of k_solve_staged and of the batched
+// staged solves).
 template <typename TW>
-__global__ void __launch_bounds__(128) k_solve_staged(TW* __restrict__ f, TW* __restrict__ w, int mline,
-                                                      int64_t lstride, int inner, int64_t outer, int64_t ostride,
-                                                      const TW* __restrict__ ta, const TW* __restrict__ tb,
-                                                      int op) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void solve_staged_lines(TW* __restrict__ f, TW* __restrict__ w, int mline,
+                                                   int64_t lstride, int inner, int64_t outer, int64_t ostride,
+                                                   const TW* __restrict__ ta, const TW* __restrict__ tb, int op,
+                                                   int64_t l0, unsigned char* smem_raw) {
   constexpr int NL = kStagedLines;
   TW* s = reinterpret_cast<TW*>(smem_raw);  // [mline][NL]
   TW* sa = s + int64_t(mline) * NL;           // [mline]
   TW* sb = sa + mline;                        // [mline]
   int64_t* off = reinterpret_cast<int64_t*>(sb + mline);  // [NL] offset of each line's first element
   const int64_t lines = int64_t(inner) * outer;
-  const int64_t l0 = int64_t(blockIdx.x) * NL;
   const int nl = int(lines - l0 < NL ? lines - l0 : NL);
   if (threadIdx.x < NL) {
     const int64_t line = l0 + (threadIdx.x < nl ? threadIdx.x : 0);
@@ -184,6 +184,16 @@ __global__ void __launch_bounds__(128) k_solve_staged(TW* __restrict__ f, TW* __
       else w[g[u]] = wv[u] - sv[u];
     }
   }
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(128) k_solve_staged(TW* __restrict__ f, TW* __restrict__ w, int mline,
+                                                      int64_t lstride, int inner, int64_t outer, int64_t ostride,
+                                                      const TW* __restrict__ ta, const TW* __restrict__ tb,
+                                                      int op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  solve_staged_lines<TW>(f, w, mline, lstride, inner, outer, ostride, ta, tb, op, int64_t(blockIdx.x) * kStagedLines,
+                         smem_raw);
 }
 
 // Lines along the contiguous axis: R rows of length mline (row pitch
