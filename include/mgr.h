@@ -261,6 +261,17 @@ int mgr_recompose_dequantized(const mgr_plan* plan, const int32_t* codes, int nc
 
 /* ------------------------------------------------------------ no-alloc form */
 
+/* Measured FP64 fused multiply-add throughput of `device`, in FMAs per second:
+   the roofline denominator of the plain FP64 form, whose level passes are
+   bound by the FP64 pipe rather than by HBM.  Every thread runs eight
+   independent FMA chains over four 256-thread CTAs per SM; the best of three
+   timed launches (after a warm-up launch, about 10 ms each on a GB300) is
+   returned in *fma_per_second (2 flops each).  The paper has no counterpart:
+   this is a measurement helper.  Synchronous; allocates and frees a small
+   device buffer; MGR_EINVAL for a bad device or a null pointer, MGR_ECUDA if
+   a CUDA call fails.  The current device is restored. */
+int mgr_fp64_fma_rate(int device, double* fma_per_second);
+
 /* Size of the fixed device scratch area used by mgr_decompose_noalloc. */
 #define MGR_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -17,7 +17,7 @@ __all__ = [
     "MGR_EDEVICE", "MGR_ENOTFOUND", "MGR_EBUSY", "MGR_F32", "MGR_F64", "MGR_PREC_NATIVE", "MGR_PREC_MIXED",
     "MgrError", "mgr_desc", "mgr_kernel_time", "mgr_request", "MGR_OP_DECOMPOSE", "MGR_OP_RECOMPOSE",
     "MGR_OP_DECOMPOSE_PACKED", "MGR_OP_RECOMPOSE_PACKED", "Server", "lib", "library_path", "Context", "Plan", "EXPORTED",
-    "PreparedBatch", "plan_tables_host",
+    "PreparedBatch", "plan_tables_host", "fp64_fma_rate",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -117,6 +117,7 @@ EXPORTED = {
     "mgr_recompose_host": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
     "mgr_decompose_noalloc": (_i, [_vp, _vp, _vp, _vp]),
+    "mgr_fp64_fma_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double)]),
     "mgr_class_offsets": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, ctypes.POINTER(_i)]),
     "mgr_decompose_packed": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mgr_recompose_packed": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
@@ -206,6 +207,13 @@ def make_desc(shape, coords=None, levels=-1, dtype=MGR_F64, prec=MGR_PREC_NATIVE
     d.dtype = int(dtype)
     d.prec = int(prec)
     return d, keep
+
+
+def fp64_fma_rate(device=0):
+    """mgr_fp64_fma_rate: measured FP64 FMAs per second of `device` (2 flops each)."""
+    v = ctypes.c_double()
+    _check("mgr_fp64_fma_rate", lib.mgr_fp64_fma_rate(int(device), ctypes.byref(v)))
+    return v.value
 
 
 def plan_tables_host(shape, coords=None, levels=-1, level=1, axis=0, dtype=MGR_F64, prec=MGR_PREC_NATIVE):

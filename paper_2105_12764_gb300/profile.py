@@ -8,6 +8,11 @@ work (mgr_profile), then the graph-replayed decompose and recompose times.
 With --plain it only runs the operations (no event brackets): a clean target
 for an external profiler.
 
+    python -m paper_2105_12764_gb300.profile --fp64-rate
+
+measures the FP64 FMA throughput of cuda:0 (mgr_fp64_fma_rate), the
+denominator of the plain FP64 form's roofline.
+
     python -m paper_2105_12764_gb300.profile --batch 4096 [--form fp32] [--reps 1]
 
 submits the batched workload (the given number of uneven 2D / 3D fields,
@@ -36,7 +41,13 @@ def main():
     ap.add_argument("--plain", action="store_true")
     ap.add_argument("--packed", action="store_true", help="class-packed decompose / recompose")
     ap.add_argument("--batch", type=int, default=0, help="batched workload of this many fields")
+    ap.add_argument("--fp64-rate", action="store_true", help="measured FP64 FMA throughput of cuda:0")
     a = ap.parse_args()
+    if a.fp64_rate:
+        rates = [mgr.fp64_fma_rate(0) for _ in range(3)]
+        print(f"FP64 FMA rate: {max(rates) / 1e12:.4f} T FMA/s = {2 * max(rates) / 1e12:.4f} TFLOP/s "
+              f"(three measurements: {', '.join(f'{r / 1e12:.4f}' for r in rates)} T FMA/s)")
+        return
     if a.batch:
         return batch_main(a)
     shape = tuple(int(v) for v in a.shape.split(","))
