@@ -272,6 +272,23 @@ int mgr_recompose_dequantized(const mgr_plan* plan, const int32_t* codes, int nc
    a CUDA call fails.  The current device is restored. */
 int mgr_fp64_fma_rate(int device, double* fma_per_second);
 
+/* Bounds-checking builds.  A library compiled with MGR_DEBUG_BOUNDS checks,
+   in every kernel of the level loop (level pass, interpolation, solves,
+   one-CTA coarse levels, coarsest copy; single-field, batched, served and 4D
+   forms), each global index against the extent of the buffer it addresses
+   and the level pass's shared-tile indices against the tile.  A violation
+   is recorded in a device error record and the access is skipped (no trap:
+   the context stays usable); the operation then waits for its stream
+   (unless the stream is being captured) and returns MGR_EDEVICE, batched
+   polls and served waits likewise.  The paper has no counterpart: this is
+   a debugging aid of this library.
+   mgr_debug_bounds: 1 in such a build, 0 otherwise.
+   mgr_debug_last: the first out-of-bounds access of the last operation that
+   returned MGR_EDEVICE -- a code naming the access, its index and the
+   buffer's extent in elements; MGR_ENOTFOUND if none was recorded. */
+int mgr_debug_bounds(void);
+int mgr_debug_last(int* code, int64_t* index, int64_t* extent);
+
 /* Size of the fixed device scratch area used by mgr_decompose_noalloc. */
 #define MGR_NOALLOC_SCRATCH_BYTES (32u << 20)
 

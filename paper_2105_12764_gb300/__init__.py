@@ -21,7 +21,9 @@ __all__ = [
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(HERE, "libmgr.so")
+# MGR_LIBRARY selects another build of the library (the bounds-checking
+# libmgr_debug.so); the default is the release build next to this file
+_LIB_PATH = os.environ.get("MGR_LIBRARY") or os.path.join(HERE, "libmgr.so")
 
 MGR_OK, MGR_EINVAL, MGR_ENOMEM, MGR_EBUDGET, MGR_ECUDA = 0, -1, -2, -3, -4
 MGR_EPENDING, MGR_ETIMEDOUT, MGR_EDEVICE, MGR_ENOTFOUND, MGR_EBUSY = -5, -6, -7, -8, -9
@@ -118,6 +120,8 @@ EXPORTED = {
     "mgr_profile": (_i, [_vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(mgr_kernel_time), _i, ctypes.POINTER(_i)]),
     "mgr_decompose_noalloc": (_i, [_vp, _vp, _vp, _vp]),
     "mgr_fp64_fma_rate": (_i, [_i, ctypes.POINTER(ctypes.c_double)]),
+    "mgr_debug_bounds": (_i, []),
+    "mgr_debug_last": (_i, [ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "mgr_class_offsets": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, ctypes.POINTER(_i)]),
     "mgr_decompose_packed": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mgr_recompose_packed": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),

@@ -3,6 +3,9 @@
 Every translation unit under ``csrc/`` is compiled for sm_103a only
 (``-gencode arch=compute_103a,code=sm_103a``) in parallel, then linked into
 one shared library with the CUDA runtime linked statically.  No cmake.
+``build(debug_bounds=True)`` builds the bounds-checking variant
+``libmgr_debug.so`` (``-DMGR_DEBUG_BOUNDS``), loaded when the environment
+variable MGR_LIBRARY names it.
 """
 import concurrent.futures as cf
 import glob
@@ -17,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgr.so")
+OBJDIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libmgr_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,18 +39,18 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
             glob.glob(os.path.join(INCLUDE, "*.h")))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, verbose_ptxas=False):
-    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+def _compile(src, verbose_ptxas=False, objdir=None, extra=()):
+    obj = os.path.join(objdir or OBJDIR, os.path.basename(src) + ".o")
+    cmd = [nvcc(), *ARCH, *extra, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
            "-c", src, "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
@@ -59,27 +64,30 @@ def _compile(src, verbose_ptxas=False):
     return obj, r.stderr
 
 
-def build(force=False, verbose_ptxas=False):
-    """Compile and link libmgr.so if any source is newer than it; return its path."""
-    if not force and not verbose_ptxas and not _stale():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force=False, verbose_ptxas=False, debug_bounds=False):
+    """Compile and link libmgr.so (or, with debug_bounds, libmgr_debug.so) if any
+    source is newer than it; return its path."""
+    lib, objdir = (LIB_DEBUG, OBJDIR_DEBUG) if debug_bounds else (LIB, OBJDIR)
+    extra = ("-DMGR_DEBUG_BOUNDS",) if debug_bounds else ()
+    if not force and not verbose_ptxas and not _stale(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose_ptxas, objdir, extra), srcs))
     if verbose_ptxas:
         for _, err in results:
             if err:
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv, debug_bounds="--debug" in sys.argv))

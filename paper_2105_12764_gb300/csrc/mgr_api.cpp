@@ -29,6 +29,47 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
   return e;
 }
 
+unsigned long long debug_take(DebugRecord* first) {
+  DebugRecord r[3] = {};
+  const unsigned long long n[3] = {debug_take_core(&r[0]), debug_take_batch(&r[1]), debug_take_st(&r[2])};
+  unsigned long long total = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (n[i] && first && total == 0) *first = r[i];
+    total += n[i];
+  }
+  return total;
+}
+
+// Bounds-checking builds: the first out-of-bounds access of the last
+// operation that reported one (mgr_debug_last).
+std::mutex g_dbg_mu;
+DebugRecord g_dbg_last{};
+bool g_dbg_have = false;
+
+// After an operation is enqueued on `st`: in bounds-checking builds wait for
+// it (unless `st` is being captured) and report a recorded out-of-bounds
+// access as MGR_EDEVICE; otherwise nothing.
+int debug_after(cudaStream_t st) {
+#ifdef MGR_DEBUG_BOUNDS
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return MGR_OK;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return MGR_ECUDA;
+  }
+  DebugRecord r{};
+  if (debug_take(&r)) {
+    std::lock_guard<std::mutex> lk(g_dbg_mu);
+    g_dbg_last = r;
+    g_dbg_have = true;
+    return MGR_EDEVICE;
+  }
+#else
+  (void)st;
+#endif
+  return MGR_OK;
+}
+
 bool fault_injected(const char* what) {
   const char* v = std::getenv("MGR_FAULT_INJECT");
   if (!v || !*v) return false;
@@ -138,6 +179,8 @@ int check_quant_args(const mgr_plan* p, const void* field, const void* codes, co
   return MGR_OK;
 }
 
+int run_op_graph(mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st, const Extra& x);
+
 // Launch through a cached CUDA graph of the plan's launch sequence.  When the
 // caller's stream is itself being captured the kernels are enqueued directly
 // (they become part of the caller's graph).
@@ -154,6 +197,12 @@ int run_op(const mgr_plan* cp, int op, const void* in, void* out, void* ws, cuda
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MGR_ECUDA;
   if (cap != cudaStreamCaptureStatusNone) return enqueue(p, op, in, out, ws, st, x) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+  const int launched = run_op_graph(p, op, in, out, ws, st, x);
+  return launched != MGR_OK ? launched : mgr::debug_after(st);
+}
+
+// The cached-graph launch of run_op.
+int run_op_graph(mgr_plan* p, int op, const void* in, void* out, void* ws, cudaStream_t st, const Extra& x) {
 
   std::lock_guard<std::mutex> lk(p->graph_mu);
   cudaGraphExec_t exec = nullptr;
@@ -248,7 +297,8 @@ int run_host_pipe(mgr_plan* p, int op, const void* host_in, void* host_out, void
     ge.dout = dev_out;
     p->graphs.push_back(ge);
   }
-  return cudaGraphLaunch(exec, st) == cudaSuccess ? MGR_OK : MGR_ECUDA;
+  if (cudaGraphLaunch(exec, st) != cudaSuccess) return MGR_ECUDA;
+  return mgr::debug_after(st);
 }
 
 int run_host(const mgr_plan* p, int op, const void* host_in, void* host_out, void* dev_in, void* dev_out, void* ws,
@@ -268,7 +318,7 @@ int run_host(const mgr_plan* p, int op, const void* host_in, void* host_out, voi
   int rc = run_op(p, op, dev_in, dev_out, ws, st);
   if (rc != MGR_OK) return rc;
   if (cudaMemcpyAsync(host_out, dev_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MGR_ECUDA;
-  return MGR_OK;
+  return mgr::debug_after(st);
 }
 
 }  // namespace
@@ -594,6 +644,23 @@ int mgr_profile(const mgr_plan* p, int op, const void* in, void* out, void* ws, 
     cudaGetLastError();
     return MGR_ECUDA;
   }
+  return mgr::debug_after(st);
+}
+
+int mgr_debug_bounds(void) {
+#ifdef MGR_DEBUG_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int mgr_debug_last(int* code, int64_t* index, int64_t* extent) {
+  std::lock_guard<std::mutex> lk(mgr::g_dbg_mu);
+  if (!mgr::g_dbg_have) return MGR_ENOTFOUND;
+  if (code) *code = mgr::g_dbg_last.code;
+  if (index) *index = mgr::g_dbg_last.index;
+  if (extent) *extent = mgr::g_dbg_last.extent;
   return MGR_OK;
 }
 

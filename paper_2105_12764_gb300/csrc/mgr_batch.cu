@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(128) kb_solve_strided(const SolveDesc<TW>* __r
     const int2 it = items[i];
     const SolveDesc<TW> s = d[it.x];
     const int64_t line = int64_t(it.y) * blockDim.x + threadIdx.x;
-    if (line < s.count) solve_strided_line<TW>(s.f, s.w, s.mline, s.lstride, s.inner, s.ostride, s.ta, s.tb, s.op, line);
+    if (line < s.count)
+      solve_strided_line<TW>(s.f, s.w, s.mline, s.lstride, s.inner, s.ostride, s.ta, s.tb, s.op, line,
+                             max(int64_t(s.mline) * s.lstride, (s.count / s.inner) * s.ostride));
   }
 }
 
@@ -1051,6 +1053,16 @@ int batch_poll(mgr_ctx* ctx, uint64_t ticket, int64_t timeout_us, int* n_done) {
     }
   }
   *n_done = n;
+#ifdef MGR_DEBUG_BOUNDS
+  // bounds-checking builds: an out-of-bounds access of the finished batch
+  DebugRecord r{};
+  if (debug_take(&r)) {
+    std::lock_guard<std::mutex> lk(g_dbg_mu);
+    g_dbg_last = r;
+    g_dbg_have = true;
+    return MGR_EDEVICE;
+  }
+#endif
   return MGR_OK;
 }
 
@@ -1077,6 +1089,27 @@ int batch_tuning(mgr_ctx* ctx, char* buf, size_t len) {
     std::snprintf(buf, len, "%s", s.c_str());
   }
   return int(s.size());
+}
+
+
+// Read and clear this translation unit's bounds-check record (MGR_DEBUG_BOUNDS).
+unsigned long long debug_take_batch(DebugRecord* first) {
+#ifdef MGR_DEBUG_BOUNDS
+  DebugRecord r{};
+  if (cudaMemcpyFromSymbol(&r, g_debug_record, sizeof(r)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (r.count) {
+    const DebugRecord zero{};
+    cudaMemcpyToSymbol(g_debug_record, &zero, sizeof(zero));
+    if (first) *first = r;
+  }
+  return r.count;
+#else
+  (void)first;
+  return 0;
+#endif
 }
 
 }  // namespace mgr

@@ -701,4 +701,25 @@ cudaError_t enqueue_recompose_dequantized(const mgr_plan* p, const int* codes, i
   }
 }
 
+
+// Read and clear this translation unit's bounds-check record (MGR_DEBUG_BOUNDS).
+unsigned long long debug_take_core(DebugRecord* first) {
+#ifdef MGR_DEBUG_BOUNDS
+  DebugRecord r{};
+  if (cudaMemcpyFromSymbol(&r, g_debug_record, sizeof(r)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (r.count) {
+    const DebugRecord zero{};
+    cudaMemcpyToSymbol(g_debug_record, &zero, sizeof(zero));
+    if (first) *first = r;
+  }
+  return r.count;
+#else
+  (void)first;
+  return 0;
+#endif
+}
+
 }  // namespace mgr

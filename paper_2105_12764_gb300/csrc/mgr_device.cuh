@@ -46,3 +46,45 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+
+// ---------------------------------------------------------------------------
+// Bounds-checking builds (MGR_DEBUG_BOUNDS): every checked access tests its
+// index against the extent of the buffer it addresses; a violation is
+// recorded in this translation unit's device record (the first one's code,
+// index and extent, and a count) and the access is skipped -- no trap, the
+// context stays usable.  The host reads and clears the record after each
+// operation and returns MGR_EDEVICE.  In other builds a check is `true` and
+// compiles away.
+// ---------------------------------------------------------------------------
+#ifdef MGR_DEBUG_BOUNDS
+static __device__ DebugRecord g_debug_record;
+__device__ __forceinline__ bool dbg_in(long long i, long long n, int code) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_debug_record.count, 1ull) == 0ull) {
+    g_debug_record.code = code;
+    g_debug_record.index = i;
+    g_debug_record.extent = n;
+  }
+  return false;
+}
+#define MGR_IN(i, n, code) dbg_in((long long)(i), (long long)(n), (code))
+#else
+#define MGR_IN(i, n, code) true
+#endif
+// pointer p inside [base, base + n)
+#define MGR_PIN(p, base, n, code) MGR_IN((p) - (base), (n), (code))
+// the statement(s) after `check`, run only where the check holds; other builds
+// run them unconditionally and do not evaluate `check` at all
+#ifdef MGR_DEBUG_BOUNDS
+#define MGR_GUARD(check, ...) \
+  do {                        \
+    if (check) {              \
+      __VA_ARGS__;            \
+    }                         \
+  } while (0)
+#else
+#define MGR_GUARD(check, ...) \
+  do {                        \
+    __VA_ARGS__;              \
+  } while (0)
+#endif

@@ -165,6 +165,37 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Device-side record of the first out-of-bounds index a bounds-checking build
+// (MGR_DEBUG_BOUNDS) met, one per translation unit with kernels; codes name
+// the access (kDbg* below).
+struct DebugRecord {
+  unsigned long long count;
+  int code;
+  int pad;
+  long long index;
+  long long extent;
+};
+enum : int {
+  kDbgLevelIn = 1, kDbgLevelY = 2, kDbgLevelW = 3, kDbgLevelF = 4, kDbgLevelStage = 5, kDbgLevelTile = 6,
+  kDbgInterpC = 11, kDbgInterpW = 12, kDbgInterpOut = 13, kDbgInterpStage = 14,
+  kDbgSolveF = 21, kDbgSolveW = 22, kDbgSolveSmem = 23,
+  kDbgSmallIn = 31, kDbgSmallOut = 32, kDbgCoarsestY = 41, kDbgCoarsestW = 42,
+};
+// Read and clear the records of every translation unit (bounds-checking
+// builds; others report nothing): returns the number of violations since the
+// last call and the first one of them in *first.
+unsigned long long debug_take(DebugRecord* first);
+unsigned long long debug_take_core(DebugRecord* first);
+unsigned long long debug_take_batch(DebugRecord* first);
+unsigned long long debug_take_st(DebugRecord* first);
+// After an operation is enqueued on `st`: bounds-checking builds wait for it
+// (unless `st` is being captured) and return MGR_EDEVICE for a recorded
+// out-of-bounds access (kept for mgr_debug_last); other builds return MGR_OK.
+int debug_after(cudaStream_t st);
+extern std::mutex g_dbg_mu;
+extern DebugRecord g_dbg_last;
+extern bool g_dbg_have;
+
 // Host-side fault injection for tests (no GPU fault is involved): true when
 // the comma-separated list in the environment variable MGR_FAULT_INJECT
 // names `what` ("alloc": device allocations of the batch / serving layers

@@ -286,6 +286,28 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   const TI* __restrict__ in = static_cast<const TI*>(a.in);
   TD* __restrict__ yout = static_cast<TD*>(a.y);
   const bool wy = (MODE == 0) && a.write_y;
+  // bounds-checking builds: extents (elements) of the buffers this CTA
+  // addresses; the LVL_* statements below check against them (other builds
+  // run the plain statements)
+#ifdef MGR_DEBUG_BOUNDS
+  const long long n_in = (PK && MODE == 1) ? (long long)nz * a.in_sz - (long long)mz * a.c_sz
+                                           : (long long)(a.in_full ? a.N[0] : nz) * a.in_sz;
+  const long long n_y = PK ? (long long)nz * a.y_sz - (long long)mz * a.c_sz : (long long)a.N[0] * a.y_sz;
+  const long long n_c = (long long)mz * a.c_sz;
+  constexpr long long n_stage = (long long)STAGES * 2 * RR * RC;
+#endif
+#define LVL_CP(dst, src) \
+  MGR_GUARD(MGR_PIN(src, in, n_in, kDbgLevelIn) && MGR_PIN(dst, stage, n_stage, kDbgLevelStage), \
+            cp_async(dst, src, int(sizeof(TI))))
+#define LVL_CPZ(dst, src, valid) \
+  MGR_GUARD(MGR_PIN(src, in, n_in, kDbgLevelIn) && MGR_PIN(dst, stage, n_stage, kDbgLevelStage), \
+            cp_async_zf(dst, src, int(sizeof(TI)), valid))
+#define LVL_Y(q, v) MGR_GUARD(MGR_PIN(q, yout, n_y, kDbgLevelY), *(q) = (v))
+#define LVL_YP(p0, p1, a0, a1, w0, w1, contig)                                                                  \
+  MGR_GUARD((!(w0) || MGR_PIN(p0, yout, n_y, kDbgLevelY)) && (!(w1) || MGR_PIN(p1, yout, n_y, kDbgLevelY)), \
+            store_pair<TD>(p0, p1, a0, a1, w0, w1, contig))
+#define LVL_W(wz, i, v) MGR_GUARD(MGR_IN((wz) - a.w + (i), n_c, kDbgLevelW), (wz)[i] = (v))
+#define LVL_F(i, v) MGR_GUARD(MGR_IN(i, n_c, kDbgLevelF), a.f[i] = (v))
   const bool afine = AF && MODE == 1 && a.all_fine;
   const TS qs = QZ ? TS(a.qs) : TS(1);
   // value written for coefficient v when `st` (the node is stored: values of
@@ -405,11 +427,30 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       const int jj = py + o - 2;
       if (jj >= 0 && jj < ny) kym[k] |= 1u << o;
     }
+    // rows past the tile's outputs (the last warp's, in all but the last tile
+    // row) are never stored: not interior, so no stencil form reads past the tile
+    if (warp * RPW + k >= nby) kym[k] = 0;
   }
   auto ky = [&](int k, int o) -> TS {
     if constexpr (weights_in_smem<TS>()) return kys[o * (NW * RPW) + warp * RPW + k];
     else return kyr[k][o];
   };
+#ifdef MGR_DEBUG_BOUNDS
+  // the shared-tile indices below are a per-thread constant plus the loop's
+  // row and tap offsets: checking the constants' ranges once covers them all
+  (void)MGR_IN(2 * (warp * RPW + RPW - 1) + 1, RR, kDbgLevelTile);  // stage / tile rows
+  (void)MGR_IN(cx0 + 1, RC, kDbgLevelTile);                           // stage / tile columns
+  if (kxo && kx_generic) {
+    (void)MGR_IN(dx - 2, RC, kDbgLevelTile);  // five x taps
+    (void)MGR_IN(dx + 2, RC, kDbgLevelTile);
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k)
+    if (kym[k] == 31u && kxo) {
+      (void)MGR_IN(dyo[k] - 2, RR, kDbgLevelTile);  // five y taps
+      (void)MGR_IN(dyo[k] + 2, RR, kDbgLevelTile);
+    }
+#endif
   __syncthreads();  // stencil weights staged
 
   auto iplane = [&](int g) -> int64_t {
@@ -425,13 +466,13 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       if (PK && MODE == 1 && zc) {
         // rows of a coarse plane: the coarse row gy0 holds its fine columns only
         const int r0 = ir0[k] - cidx(gy0[k]) * mx, r1 = ir1[k] - cidx(gy0[k] + 1) * mx;
-        if (vy0[k] && fx1) cp_async(d0 + 1, base + r0 + pcx1, int(sizeof(TI)));
+        if (vy0[k] && fx1) LVL_CP(d0 + 1, base + r0 + pcx1);
         if (vy1[k]) {
           if (fy1[k]) {
-            if (vx0) cp_async(d0 + RC, base + r1 + ic0, int(sizeof(TI)));
-            if (vx1) cp_async(d0 + RC + 1, base + r1 + ic1, int(sizeof(TI)));
+            if (vx0) LVL_CP(d0 + RC, base + r1 + ic0);
+            if (vx1) LVL_CP(d0 + RC + 1, base + r1 + ic1);
           } else if (fx1) {
-            cp_async(d0 + RC + 1, base + r1 + pcx1, int(sizeof(TI)));
+            LVL_CP(d0 + RC + 1, base + r1 + pcx1);
           }
         }
         continue;
@@ -439,20 +480,20 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       if constexpr (MODE == 1) {
         // branch-free: every slot is copied, slots outside the region as zeros
         // (their addresses are clamped into the grid, so they are valid)
-        cp_async_zf(d0, base + ir0[k] + ic0, int(sizeof(TI)), vy0[k] && vx0);
-        cp_async_zf(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)), vy0[k] && vx1);
-        cp_async_zf(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)), vy1[k] && vx0);
-        cp_async_zf(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)), vy1[k] && vx1);
+        LVL_CPZ(d0, base + ir0[k] + ic0, vy0[k] && vx0);
+        LVL_CPZ(d0 + 1, base + ir0[k] + ic1, vy0[k] && vx1);
+        LVL_CPZ(d0 + RC, base + ir1[k] + ic0, vy1[k] && vx0);
+        LVL_CPZ(d0 + RC + 1, base + ir1[k] + ic1, vy1[k] && vx1);
       } else {
         // (the decomposition pass is short of registers: copying only the slots
         // inside the region keeps its per-slot predicates out of the loop)
         if (vy0[k]) {
-          if (vx0) cp_async(d0, base + ir0[k] + ic0, int(sizeof(TI)));
-          if (vx1) cp_async(d0 + 1, base + ir0[k] + ic1, int(sizeof(TI)));
+          if (vx0) LVL_CP(d0, base + ir0[k] + ic0);
+          if (vx1) LVL_CP(d0 + 1, base + ir0[k] + ic1);
         }
         if (vy1[k]) {
-          if (vx0) cp_async(d0 + RC, base + ir1[k] + ic0, int(sizeof(TI)));
-          if (vx1) cp_async(d0 + RC + 1, base + ir1[k] + ic1, int(sizeof(TI)));
+          if (vx0) LVL_CP(d0 + RC, base + ir1[k] + ic0);
+          if (vx1) LVL_CP(d0 + RC + 1, base + ir1[k] + ic1);
         }
       }
     }
@@ -605,30 +646,30 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       if (PK && wy && own_c) {
         // packed class: the coarse row gy0 keeps only its fine column gx1
         const int r0 = yr0[k] - cidx(gy0[k]) * mx, r1 = yr1[k] - cidx(gy0[k] + 1) * mx;
-        if (owy0[k] && owx1 && fx1) yzc[r0 + pcx1] = yval(c[1], true);
+        if (owy0[k] && owx1 && fx1) LVL_Y(yzc + r0 + pcx1, yval(c[1], true));
         if (owy1[k]) {
           if (fy1[k]) {
-            store_pair<TD>(yzc + r1 + yc0, yzc + r1 + yc1, yval(c[2], owx0), yval(c[3], owx1), owx0, owx1, true);
+            LVL_YP(yzc + r1 + yc0, yzc + r1 + yc1, yval(c[2], owx0), yval(c[3], owx1), owx0, owx1, true);
           } else if (owx1 && fx1) {
-            yzc[r1 + pcx1] = yval(c[3], true);
+            LVL_Y(yzc + r1 + pcx1, yval(c[3], true));
           }
         }
       } else if (!RS && wy && own_c) {
         // all-coarse nodes get their (uncorrected) value as a placeholder that a
         // coarser level overwrites; it keeps the row's sectors fully written
-        store_pair<TD>(yzc + yr0[k] + yc0, yzc + yr0[k] + yc1, TD(vc[k][0]), TD(fx1 ? c[1] : vc[k][1]),
+        LVL_YP(yzc + yr0[k] + yc0, yzc + yr0[k] + yc1, TD(vc[k][0]), TD(fx1 ? c[1] : vc[k][1]),
                        owy0[k] && owx0, owy0[k] && owx1, ycontig);
-        store_pair<TD>(yzc + yr1[k] + yc0, yzc + yr1[k] + yc1, TD(fy1[k] ? c[2] : vc[k][2]),
+        LVL_YP(yzc + yr1[k] + yc0, yzc + yr1[k] + yc1, TD(fy1[k] ? c[2] : vc[k][2]),
                        TD((fx1 || fy1[k]) ? c[3] : vc[k][3]), owy1[k] && owx0, owy1[k] && owx1, ycontig);
       }
       if (MODE == 0 && own_c) {
         // coarse nodal values of the owned all-coarse nodes
         TW* wz = a.w + int64_t(t) * a.c_sz;
-        if (owy0[k] && owx0) wz[int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx0)] = TW(rc[k][0]);
-        if (owy0[k] && owx1 && !fx1) wz[int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx1)] = TW(rc[k][1]);
+        if (owy0[k] && owx0) LVL_W(wz, int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx0), TW(rc[k][0]));
+        if (owy0[k] && owx1 && !fx1) LVL_W(wz, int64_t(cidx(gy0[k])) * a.c_sy + cidx(gx1), TW(rc[k][1]));
         if (owy1[k] && !fy1[k]) {
-          if (owx0) wz[int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx0)] = TW(rc[k][2]);
-          if (owx1 && !fx1) wz[int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx1)] = TW(rc[k][3]);
+          if (owx0) LVL_W(wz, int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx0), TW(rc[k][2]));
+          if (owx1 && !fx1) LVL_W(wz, int64_t(cidx(gy0[k] + 1)) * a.c_sy + cidx(gx1), TW(rc[k][3]));
         }
       }
       if (hf) {
@@ -659,9 +700,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
         *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
         if (!RS && wy && own_f) {
-          store_pair<TD>(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, yval(d[0], owy0[k] && owx0), yval(d[1], owy0[k] && owx1), owy0[k] && owx0,
+          LVL_YP(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, yval(d[0], owy0[k] && owx0), yval(d[1], owy0[k] && owx1), owy0[k] && owx0,
                          owy0[k] && owx1, ycontig);
-          store_pair<TD>(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, yval(d[2], owy1[k] && owx0), yval(d[3], owy1[k] && owx1), owy1[k] && owx0,
+          LVL_YP(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, yval(d[2], owy1[k] && owx0), yval(d[3], owy1[k] && owx1), owy1[k] && owx0,
                          owy1[k] && owx1, ycontig);
         }
       } else if constexpr (BF) {
@@ -685,12 +726,12 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
             const bool orow = h == 0 ? owy0[k] : owy1[k];
             const int yr = h == 0 ? yr0[k] : yr1[k];
             if (orow && own_c) {
-              if (rs0) yzc[yr + ro0] = TD(cc[r * CP + rsl0]);
-              if (rs1) yzc[yr + ro1] = TD(cc[r * CP + rsl1]);
+              if (rs0) LVL_Y(yzc + yr + ro0, TD(cc[r * CP + rsl0]));
+              if (rs1) LVL_Y(yzc + yr + ro1, TD(cc[r * CP + rsl1]));
             }
             if (orow && own_f) {
-              if (rs0) yzf[yr + ro0] = TD(cf[r * CP + rsl0]);
-              if (rs1) yzf[yr + ro1] = TD(cf[r * CP + rsl1]);
+              if (rs0) LVL_Y(yzf + yr + ro0, TD(cf[r * CP + rsl0]));
+              if (rs1) LVL_Y(yzf + yr + ro1, TD(cf[r * CP + rsl1]));
             }
           }
         }
@@ -817,7 +858,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         acc0[k] += wzf[0] * gf;
         acc1[k] += wzf[1] * gf;
         if (j < nby && kxo && t - 1 >= qz0 && t - 1 < qz1)
-          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
+          LVL_F(int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
       } else if (j < nby && kxo) {
         TS gc = TS(0), gf = TS(0);
         const TS* gcol = gxb + (dyo[k] - 2) * 32 + lane;
@@ -846,7 +887,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           acc1[k] += wzf[1] * gf;
         }
         if (t - 1 >= qz0 && t - 1 < qz1)
-          a.f[int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
+          LVL_F(int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
       }
       acc0[k] = acc1[k];
       acc1[k] = acc2[k];
@@ -859,10 +900,17 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int j = warp * RPW + k;
-      if (j < nby && kxo) a.f[int64_t(mz - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo] = fout(acc0[k]);
+      if (j < nby && kxo) LVL_F(int64_t(mz - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
     }
   }
 }
+
+#undef LVL_CP
+#undef LVL_CPZ
+#undef LVL_Y
+#undef LVL_YP
+#undef LVL_W
+#undef LVL_F
 
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_level(const LevelArgs<TS, TW> a) {
@@ -928,6 +976,24 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     else return TS(v) + b;
   };
   TO* __restrict__ out = static_cast<TO*>(a.out);
+  // bounds-checking builds: extents of the buffers; the ITP_* statements
+  // check against them (other builds run the plain statements)
+#ifdef MGR_DEBUG_BOUNDS
+  const long long n_ci = PK ? (long long)nz * a.y_sz - (long long)mz * a.c_sz : (long long)a.N[0] * a.y_sz;
+  const long long n_w = (long long)mz * a.c_sz;
+  const long long n_o = (long long)(a.out_full ? a.N[0] : nz) * a.o_sz;
+  constexpr long long n_stage = 2LL * 2 * RR * RC;
+#endif
+#define ITP_CP(dst, src) \
+  MGR_GUARD(MGR_PIN(src, cin, n_ci, kDbgInterpC) && MGR_PIN(dst, stage, n_stage, kDbgInterpStage), \
+            cp_async(dst, src, int(sizeof(TD))))
+#define ITP_LP(dst, s0, s1, v0, v1, contig)                                                                          \
+  MGR_GUARD((!(v0) || MGR_PIN(s0, cin, n_ci, kDbgInterpC)) && (!(v1) || MGR_PIN(s1, cin, n_ci, kDbgInterpC)) && \
+                MGR_PIN((dst) + 1, stage, n_stage, kDbgInterpStage),                                              \
+            load_pair(dst, s0, s1, v0, v1, contig))
+#define ITP_OP(p0, p1, a0, a1, w0, w1, contig)                                                                          \
+  MGR_GUARD((!(w0) || MGR_PIN(p0, out, n_o, kDbgInterpOut)) && (!(w1) || MGR_PIN(p1, out, n_o, kDbgInterpOut)), \
+            store_pair<TO>(p0, p1, a0, a1, w0, w1, contig))
 
   // column block of this lane: fine nodes p(qx) and, when a fine node lies
   // between qx and qx+1, p(qx)+1
@@ -977,13 +1043,13 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
         if (!ay[k]) continue;
         if (zc) {
           // the coarse row g0 of a coarse plane holds its fine column only
-          if (ox1) cp_async(sb + r0 * RC + 2 * lane + 1, base + crc0[k] + pcx1, int(sizeof(TD)));
+          if (ox1) ITP_CP(sb + r0 * RC + 2 * lane + 1, base + crc0[k] + pcx1);
           if (oy1[k])
-            load_pair(sb + (r0 + 1) * RC + 2 * lane, base + crc1[k] + cc0, base + crc1[k] + cc1, ax, ox1, true);
+            ITP_LP(sb + (r0 + 1) * RC + 2 * lane, base + crc1[k] + cc0, base + crc1[k] + cc1, ax, ox1, true);
         } else {
-          load_pair(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, true);
+          ITP_LP(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, true);
           if (oy1[k])
-            load_pair(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, true);
+            ITP_LP(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, true);
         }
       }
       return;
@@ -993,8 +1059,8 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     for (int k = 0; k < RPW; ++k) {
       const int r0 = 2 * (warp * RPW + k);
       if (ay[k]) {
-        load_pair(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, ccontig);
-        if (oy1[k]) load_pair(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, ccontig);
+        ITP_LP(sb + r0 * RC + 2 * lane, base + cr0[k] + cc0, base + cr0[k] + cc1, ax, ox1, ccontig);
+        if (oy1[k]) ITP_LP(sb + (r0 + 1) * RC + 2 * lane, base + cr1[k] + cc0, base + cr1[k] + cc1, ax, ox1, ccontig);
       }
     }
   };
@@ -1004,7 +1070,9 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     const TW* src = a.w + int64_t(t) * a.c_sz + int64_t(qy0) * a.c_sy + qx0;
     for (int e = threadIdx.x; e < trows * TC; e += NW * 32) {
       const int r = e / TC, cix = e - r * TC;
-      if (cix < tcols) cp_async(tb + r * TC + cix, src + int64_t(r) * a.c_sy + cix, int(sizeof(TW)));
+      if (cix < tcols)
+        MGR_GUARD(MGR_PIN(src + int64_t(r) * a.c_sy + cix, a.w, n_w, kDbgInterpW),
+                  cp_async(tb + r * TC + cix, src + int64_t(r) * a.c_sy + cix, int(sizeof(TW))));
     }
     TD* sb = stage + st * 2 * RR * RC;
     if (t < qz1) load_c(sb, pidx(t, nz), true);
@@ -1070,20 +1138,20 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
       }
       if (act && own_c) {
         const TD2 c0 = ldc(sc + r0 * RC + 2 * lane);
-        store_pair<TO>(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(cadd(c0.y, In[k][1])), true, ox1, ocontig);
+        ITP_OP(ozc + or0[k] + oc0, ozc + or0[k] + oc1, TO(w00r), TO(cadd(c0.y, In[k][1])), true, ox1, ocontig);
         if (oy1[k]) {
           const TD2 c1 = ldc(sc + (r0 + 1) * RC + 2 * lane);
-          store_pair<TO>(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(cadd(c1.x, In[k][2])), TO(cadd(c1.y, In[k][3])),
+          ITP_OP(ozc + or1[k] + oc0, ozc + or1[k] + oc1, TO(cadd(c1.x, In[k][2])), TO(cadd(c1.y, In[k][3])),
                          true, ox1, ocontig);
         }
       }
       if (act && hf) {
         const TD2 c0 = ldc(sf + r0 * RC + 2 * lane);
-        store_pair<TO>(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(QZ ? cadd(c0.x, za * Ip[k][0] + zb * In[k][0]) : TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
+        ITP_OP(ozf + or0[k] + oc0, ozf + or0[k] + oc1, TO(QZ ? cadd(c0.x, za * Ip[k][0] + zb * In[k][0]) : TS(c0.x) + za * Ip[k][0] + zb * In[k][0]),
                        TO(QZ ? cadd(c0.y, za * Ip[k][1] + zb * In[k][1]) : TS(c0.y) + za * Ip[k][1] + zb * In[k][1]), true, ox1, ocontig);
         if (oy1[k]) {
           const TD2 c1 = ldc(sf + (r0 + 1) * RC + 2 * lane);
-          store_pair<TO>(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(QZ ? cadd(c1.x, za * Ip[k][2] + zb * In[k][2]) : TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
+          ITP_OP(ozf + or1[k] + oc0, ozf + or1[k] + oc1, TO(QZ ? cadd(c1.x, za * Ip[k][2] + zb * In[k][2]) : TS(c1.x) + za * Ip[k][2] + zb * In[k][2]),
                          TO(QZ ? cadd(c1.y, za * Ip[k][3] + zb * In[k][3]) : TS(c1.y) + za * Ip[k][3] + zb * In[k][3]), true, ox1, ocontig);
         }
       }
@@ -1093,6 +1161,10 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     __syncthreads();  // both stage buffers are reloaded two iterations later
   }
 }
+
+#undef ITP_CP
+#undef ITP_LP
+#undef ITP_OP
 
 template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK, bool QZ>
 __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_interp(const InterpArgs<TS, TW> a) {

@@ -98,5 +98,5 @@ extern "C" int mgr_decompose_noalloc(const mgr_plan* plan, const void* in, void*
     cudaGetLastError();
     return MGR_ECUDA;
   }
-  return MGR_OK;
+  return mgr::debug_after(st);
 }

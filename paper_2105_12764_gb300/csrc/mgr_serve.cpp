@@ -320,6 +320,18 @@ int mgr_serve_wait(mgr_server* s, uint64_t id, int64_t timeout_us, mgr_serve_res
     }
   }
   res->status = r->rc;
+#ifdef MGR_DEBUG_BOUNDS
+  // bounds-checking builds: an out-of-bounds access of the finished request
+  if (r->rc == MGR_OK) {
+    mgr::DebugRecord rec{};
+    if (mgr::debug_take(&rec)) {
+      std::lock_guard<std::mutex> dl(mgr::g_dbg_mu);
+      mgr::g_dbg_last = rec;
+      mgr::g_dbg_have = true;
+      res->status = MGR_EDEVICE;
+    }
+  }
+#endif
   res->arrival = r->t_arrival;
   res->admitted = r->t_admit;
   res->done = r->t_done;

@@ -57,6 +57,21 @@ __device__ __forceinline__ int64_t small_full(const int64_t* s, const int64_t* N
   return fmap(i0, s[0], N[0]) * sz + fmap(i1, s[1], N[1]) * sy + fmap(i2, s[2], N[2]);
 }
 
+// Full-grid element i of a field (N[0] * sz elements): read, and write, checked
+// in bounds-checking builds.
+template <typename T>
+__device__ __forceinline__ T small_ld(const T* p, int64_t i, const int64_t* N, int64_t sz) {
+  (void)N;
+  (void)sz;
+  return MGR_IN(i, N[0] * sz, kDbgSmallIn) ? p[i] : T(0);
+}
+template <typename T>
+__device__ __forceinline__ void small_st(T* p, int64_t i, T v, const int64_t* N, int64_t sz) {
+  (void)N;
+  (void)sz;
+  if (MGR_IN(i, N[0] * sz, kDbgSmallOut)) p[i] = v;
+}
+
 // (P_0 x P_1 x P_2) W at level node (i0, i1, i2): the multilinear interpolant
 // of the coarse values around it (one or two coarse neighbours per axis).
 template <typename TS, typename TW>
@@ -186,7 +201,7 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
     for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
       if (a.vin_full) {
         const int i2 = int(e % n2), i1 = int((e / n2) % n1), i0 = int(e / (int64_t(n1) * n2));
-        V[e] = TW(static_cast<const TD*>(a.vin)[small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy)]);
+        V[e] = TW(small_ld(static_cast<const TD*>(a.vin), small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
       } else {
         V[e] = static_cast<const TW*>(a.vin)[e];
       }
@@ -212,7 +227,7 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
       }
       const TS c = TS(V[e]) - small_interp<TS, TW>(W, n, m, a.wa[l], a.wb[l], i0, i1, i2);
       V[e] = TW(c);
-      out[small_full(a.s[l], a.N, i0, i1, i2, a.sz, a.sy)] = TD(c);
+      small_st(out, small_full(a.s[l], a.N, i0, i1, i2, a.sz, a.sy), TD(c), a.N, a.sz);
     }
     __syncthreads();
     small_load_vector<TS, TW>(V, T1, T2, F, n, m, a.k[l]);
@@ -225,7 +240,7 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
   const int c0 = a.n0[0], c1 = a.n0[1], c2 = a.n0[2];
   for (int e = threadIdx.x; e < c0 * c1 * c2; e += blockDim.x) {
     const int i2 = e % c2, i1 = (e / c2) % c1, i0 = e / (c1 * c2);
-    out[small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy)] = TD(V[e]);
+    small_st(out, small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy), TD(V[e]), a.N, a.sz);
   }
 }
 
@@ -252,7 +267,7 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
     const int c0 = a.n0[0], c1 = a.n0[1], c2 = a.n0[2];
     for (int e = threadIdx.x; e < c0 * c1 * c2; e += blockDim.x) {
       const int i2 = e % c2, i1 = (e / c2) % c1, i0 = e / (c1 * c2);
-      W[e] = TW(cin[small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy)]);
+      W[e] = TW(small_ld(cin, small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
     }
   }
   __syncthreads();
@@ -264,7 +279,7 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
     for (int e = threadIdx.x; e < ln; e += blockDim.x) {
       const int i2 = e % n[2], i1 = (e / n[2]) % n[1], i0 = e / (n[1] * n[2]);
       const bool coarse = is_coarse(i0, n[0]) && is_coarse(i1, n[1]) && is_coarse(i2, n[2]);
-      V[e] = coarse ? TW(0) : TW(cin[small_full(a.s[l], a.N, i0, i1, i2, a.sz, a.sy)]);
+      V[e] = coarse ? TW(0) : TW(small_ld(cin, small_full(a.s[l], a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
     }
     __syncthreads();
     small_load_vector<TS, TW>(V, T1, T2, F, n, m, a.k[l]);
@@ -291,7 +306,7 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
   for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
     if (a.vout_full) {
       const int i2 = int(e % n2), i1 = int((e / n2) % n1), i0 = int(e / (int64_t(n1) * n2));
-      static_cast<TD*>(a.vout)[small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy)] = TD(V[e]);
+      small_st(static_cast<TD*>(a.vout), small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy), TD(V[e]), a.N, a.sz);
     } else {
       static_cast<TW*>(a.vout)[e] = V[e];
     }

@@ -27,9 +27,14 @@ __device__ __forceinline__ void apply_op(TW* f, TW* w, int64_t g, TW v, int op) 
 template <typename TW, int U = 8>
 __device__ __forceinline__ void solve_strided_line(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t lstride,
                                                    int inner, int64_t ostride, const TW* __restrict__ ta,
-                                                   const TW* __restrict__ tb, int op, int64_t line) {
+                                                   const TW* __restrict__ tb, int op, int64_t line,
+                                                   long long ext = 0) {
+  (void)ext;  // elements of f and w (the coarse grid): checked in bounds-checking builds
   const int i = int(line % inner);
   const int64_t o = line / inner;
+  // the line's elements are o*ostride + i + q*lstride, q = 0..mline-1: its ends bound them all
+  if (!MGR_IN(o * ostride + i, ext, kDbgSolveF) || !MGR_IN(o * ostride + i + int64_t(mline - 1) * lstride, ext, kDbgSolveF))
+    return;
   TW* fl = f + o * ostride + i;
   TW prev = TW(0);
   for (int q0 = 0; q0 < mline; q0 += U) {
@@ -77,7 +82,8 @@ __global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* _
   if (id >= int64_t(inner) * outer) return;
   // 64 bytes of loads in flight per thread and sweep: sixteen FP32 or eight FP64 elements
   // (sixteen FP64 elements cost occupancy and were slower)
-  solve_strided_line<TW, sizeof(TW) == 4 ? 16 : 8>(f, w, mline, lstride, inner, ostride, ta, tb, op, id);
+  solve_strided_line<TW, sizeof(TW) == 4 ? 16 : 8>(f, w, mline, lstride, inner, ostride, ta, tb, op, id,
+                                                   max(int64_t(mline) * lstride, outer * ostride));
 }
 
 // Lines along a strided axis, 32 per CTA, staged whole in shared memory: the
@@ -113,7 +119,16 @@ __device__ __forceinline__ void solve_staged_lines(TW* __restrict__ f, TW* __res
   if (threadIdx.x < NL) {
     const int64_t line = l0 + (threadIdx.x < nl ? threadIdx.x : 0);
     const int64_t o = line / inner;
-    off[threadIdx.x] = o * ostride + (line - o * inner);
+    const int64_t first = o * ostride + (line - o * inner);
+#ifdef MGR_DEBUG_BOUNDS
+    // a line's elements are first + q*lstride: its ends bound them all (out of
+    // bounds: recorded, and the line is pointed at element 0 to stay inside)
+    const long long ext = max(int64_t(mline) * lstride, outer * ostride);
+    const bool ok = MGR_IN(first, ext, kDbgSolveF) && MGR_IN(first + int64_t(mline - 1) * lstride, ext, kDbgSolveF);
+    off[threadIdx.x] = ok ? first : 0;
+#else
+    off[threadIdx.x] = first;
+#endif
   }
   for (int q = threadIdx.x; q < mline; q += blockDim.x) {
     sa[q] = ta[q];
@@ -217,6 +232,8 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
   TW* sa = s + R * pitch;                   // [mline]
   TW* sb = sa + mline;                      // [mline]
   const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
+  // rows r0 .. r0+nr-1 of mline elements at pitch row_pitch
+  if (!MGR_IN((r0 + nr - 1) * row_pitch + mline - 1, rows * row_pitch, kDbgSolveF)) return;
   const int total = nr * mline;
   // the rows go to shared memory as element-wise asynchronous copies, all in
   // flight at once (the staging, not the recurrences, bounds this kernel)
@@ -317,6 +334,8 @@ __global__ void __launch_bounds__(kRowsWarps * 32) k_solve_rows(TW* __restrict__
   const int64_t r0 = (int64_t(blockIdx.x) * kRowsWarps + warp) * 32;
   if (r0 >= rows) return;
   const int nr = int(rows - r0 < 32 ? rows - r0 : 32);
+  // rows r0 .. r0+nr-1 of mline elements at pitch row_pitch
+  if (!MGR_IN((r0 + nr - 1) * row_pitch + mline - 1, rows * row_pitch, kDbgSolveF)) return;
   TW(*tile)[33] = tiles[warp];
   TW* base = f + r0 * row_pitch;
   TW* wb = w + r0 * row_pitch;
@@ -392,6 +411,7 @@ __device__ __forceinline__ void coarsest_copy(TD* y, int64_t y_sz, int64_t y_sy,
     const int64_t rest = e / n.z;
     const int gy = int(rest % n.y), gz = int(rest / n.y);
     const int64_t yo = fmap(gz, s.x, N.x) * y_sz + fmap(gy, s.y, N.y) * y_sy + fmap(gx, s.z, N.z);
+    if (!MGR_IN(yo, N.x * y_sz, kDbgCoarsestY)) continue;
     if (dir == 0) w[e] = TW(y[yo]);
     else y[yo] = TD(w[e]);
   }

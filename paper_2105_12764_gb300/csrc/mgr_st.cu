@@ -527,4 +527,25 @@ cudaError_t enqueue_recompose_st(const mgr_plan* p, const void* in, void* out, v
   }
 }
 
+
+// Read and clear this translation unit's bounds-check record (MGR_DEBUG_BOUNDS).
+unsigned long long debug_take_st(DebugRecord* first) {
+#ifdef MGR_DEBUG_BOUNDS
+  DebugRecord r{};
+  if (cudaMemcpyFromSymbol(&r, g_debug_record, sizeof(r)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (r.count) {
+    const DebugRecord zero{};
+    cudaMemcpyToSymbol(g_debug_record, &zero, sizeof(zero));
+    if (first) *first = r;
+  }
+  return r.count;
+#else
+  (void)first;
+  return 0;
+#endif
+}
+
 }  // namespace mgr

@@ -101,3 +101,21 @@ def test_class_offsets_match_oracle_without_device():
         expect = np.cumsum([0, cnt[0]] + [cnt[l] - cnt[l - 1] for l in range(1, L + 1)])
         if np.prod(shape) < 5e6:
             np.testing.assert_array_equal(oracle.class_offsets(shape, L), expect)
+
+
+def test_bounds_checking_variant_exports_the_same_abi(lib_path):
+    """libmgr_debug.so (MGR_DEBUG_BOUNDS) exports every declared symbol and says
+    it checks; the release build says it does not (no GPU needed for either)."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("mgr_build2", os.path.join(ROOT, "paper_2105_12764_gb300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    dbg = ctypes.CDLL(b.build(debug_bounds=True))
+    missing = [n for n in declared() if not hasattr(dbg, n)]
+    assert not missing, missing
+    assert dbg.mgr_debug_bounds() == 1
+    assert ctypes.CDLL(lib_path).mgr_debug_bounds() == 0
+    code = ctypes.c_int()
+    idx, ext = ctypes.c_int64(), ctypes.c_int64()
+    assert dbg.mgr_debug_last(ctypes.byref(code), ctypes.byref(idx), ctypes.byref(ext)) == -8  # MGR_ENOTFOUND
