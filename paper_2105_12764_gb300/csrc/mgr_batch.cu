@@ -29,6 +29,7 @@
 #include <chrono>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -780,6 +781,7 @@ struct BatchState {
   // autotune decisions keyed by the batch shape
   std::map<std::string, TileCand> tuned;
   std::map<std::string, std::vector<std::pair<TileCand, double>>> tune_log;
+  std::map<std::string, bool> from_file;  // decision read from the persisted cache
 };
 
 namespace {
@@ -826,10 +828,74 @@ double time_candidate(mgr_ctx* ctx, const std::vector<FieldRef>& fields, int op,
   return ms;
 }
 
+// Persisted decisions: the environment variable MGR_AUTOTUNE_CACHE names a
+// text file of lines "<gpu> <shape> <tile> <chunk>" -- the GPU as its name
+// (spaces as '_') and SM count, the batch shape as the FNV-1a hash of its key
+// (operation, form, every field's shape and depth), the tile shape index and
+// the chunk length.  A decision found there is used without timing; a new
+// one is appended.  Read and written on each tuning (no file: nothing kept).
+std::string gpu_key(int device) {
+  cudaDeviceProp pr{};
+  if (cudaGetDeviceProperties(&pr, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string k = pr.name;
+  for (char& ch : k)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  return k + "_sm" + std::to_string(pr.multiProcessorCount);
+}
+
+unsigned long long shape_hash(const std::string& skey) {
+  unsigned long long h = 1469598103934665603ull;
+  for (unsigned char ch : skey) {
+    h ^= ch;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+bool cache_lookup(const char* path, const std::string& gk, unsigned long long h, TileCand* out) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char g[256];
+  unsigned long long hh = 0;
+  int cfg = 0, chunk = 0;
+  bool found = false;
+  while (std::fscanf(f, "%255s %llx %d %d", g, &hh, &cfg, &chunk) == 4) {
+    if (gk == g && hh == h && cfg >= 0 && cfg < kNumCfg && (chunk == 8 || chunk == 16 || chunk == 32)) {
+      *out = TileCand{cfg, chunk};  // the last matching line wins
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& gk, unsigned long long h, TileCand c) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %llx %d %d\n", gk.c_str(), h, c.cfg, c.chunk);
+  std::fclose(f);
+}
+
 template <typename TD, typename TS, typename TW>
 TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fields, int op, const std::string& skey) {
   auto it = B.tuned.find(skey);
   if (it != B.tuned.end()) return it->second;
+  const char* path = std::getenv("MGR_AUTOTUNE_CACHE");
+  const bool persist = path && *path;
+  const std::string gk = persist ? gpu_key(ctx->device) : std::string();
+  const unsigned long long h = persist ? shape_hash(skey) : 0ull;
+  if (persist) {
+    TileCand c{};
+    if (cache_lookup(path, gk, h, &c)) {
+      B.tuned[skey] = c;
+      B.tune_log[skey] = {};
+      B.from_file[skey] = true;
+      return c;
+    }
+  }
   std::vector<std::pair<double, TileCand>> ranked;
   for (int cfg = 0; cfg < kNumCfg; ++cfg)
     for (int chunk : {8, 16, 32}) {
@@ -866,6 +932,7 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
   }
   B.tuned[skey] = best;
   B.tune_log[skey] = log;
+  if (persist) cache_store(path, gk, h, best);
   return best;
 }
 
@@ -1075,7 +1142,8 @@ int batch_tuning(mgr_ctx* ctx, char* buf, size_t len) {
       s += "shape[" + std::to_string(kv.first.size()) + " chars]";
       const TileCand c = B->tuned[kv.first];
       char line[128];
-      std::snprintf(line, sizeof(line), " chosen tile=%s chunk=%d;", c.cfg == 0 ? "30x14" : "30x6", c.chunk);
+      std::snprintf(line, sizeof(line), " chosen tile=%s chunk=%d;%s", c.cfg == 0 ? "30x14" : "30x6", c.chunk,
+                    B->from_file.count(kv.first) ? " (from the persisted cache)" : "");
       s += line;
       for (auto& m : kv.second) {
         std::snprintf(line, sizeof(line), " [%s/%d: %.3f ms]", m.first.cfg == 0 ? "30x14" : "30x6", m.first.chunk,

@@ -104,3 +104,34 @@ def test_batch_errors(ctx):
     small.close()
     p64.close()
     p32.close()
+
+
+def test_autotune_decision_persists_across_contexts(tmp_path, monkeypatch):
+    """MGR_AUTOTUNE_CACHE: the first context times the candidates and appends its
+    decision, keyed by GPU and batch shape; a later context (another process
+    would be the same) reads it instead of timing, and computes the same result."""
+    path = tmp_path / "autotune.txt"
+    monkeypatch.setenv("MGR_AUTOTUNE_CACHE", str(path))
+    rng = np.random.default_rng(21)
+    fields = make_fields(rng, 8, mgr.MGR_F32)
+    results = []
+    for round_ in range(2):
+        c = mgr.Context(0)
+        plans = [mgr.Plan(c, u.shape, coords, -1, mgr.MGR_F32) for u, coords in fields]
+        ins = [torch.from_numpy(u).cuda() for u, _ in fields]
+        outs = [torch.empty_like(x) for x in ins]
+        t = c.batch_submit([(mgr.MGR_OP_DECOMPOSE, p, a, b) for p, a, b in zip(plans, ins, outs)])
+        assert c.batch_poll(t, -1)[0] == mgr.MGR_OK
+        report = c.batch_tuning()
+        assert ("from the persisted cache" in report) == (round_ == 1), report
+        if round_ == 0:
+            lines = path.read_text().split("\n")
+            assert len([ln for ln in lines if ln.strip()]) == 1
+            name = torch.cuda.get_device_name(0).replace(" ", "_")
+            assert lines[0].startswith(name)
+        results.append([o.cpu().numpy() for o in outs])
+        for p in plans:
+            p.close()
+        c.close()
+    for a, b in zip(*results):
+        np.testing.assert_array_equal(a, b)
