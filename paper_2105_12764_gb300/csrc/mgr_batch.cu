@@ -99,6 +99,16 @@ struct SolveDesc {
   int mline, inner, op, R;
 };
 
+// Elements of a line loaded ahead of the recurrence per thread in the batched
+// strided solves (build-time tunable).
+#ifndef MGR_BATCH_SOLVE_U32
+#define MGR_BATCH_SOLVE_U32 8
+#endif
+template <typename TW>
+constexpr int kBatchSolveU() {
+  return sizeof(TW) == 4 ? MGR_BATCH_SOLVE_U32 : 8;
+}
+
 template <typename TW>
 __global__ void __launch_bounds__(128) kb_solve_strided(const SolveDesc<TW>* __restrict__ d,
                                                         const int2* __restrict__ items, int n) {
@@ -107,7 +117,8 @@ __global__ void __launch_bounds__(128) kb_solve_strided(const SolveDesc<TW>* __r
     const SolveDesc<TW> s = d[it.x];
     const int64_t line = int64_t(it.y) * blockDim.x + threadIdx.x;
     if (line < s.count)
-      solve_strided_line<TW>(s.f, s.w, s.mline, s.lstride, s.inner, s.ostride, s.ta, s.tb, s.op, line,
+      solve_strided_line<TW, kBatchSolveU<TW>()>(s.f, s.w, s.mline, s.lstride, s.inner, s.ostride, s.ta, s.tb, s.op,
+                                                 line,
                              max(int64_t(s.mline) * s.lstride, (s.count / s.inner) * s.ostride));
   }
 }
@@ -128,10 +139,17 @@ __global__ void __launch_bounds__(128) kb_solve_contig(const SolveDesc<TW>* __re
 // The coarse end of every field's hierarchy (its levels of at most a few
 // thousand nodes), one field per CTA: the one-CTA coarse-level bodies of the
 // single-field path, over a list of fields (largest first).
-constexpr int kBatchSmallThreads = 512;
+#ifndef MGR_BATCH_SMALL_THREADS
+#define MGR_BATCH_SMALL_THREADS 256
+#endif
+#ifndef MGR_BATCH_SMALL_SMEM_KB
+#define MGR_BATCH_SMALL_SMEM_KB 50
+#endif
+constexpr int kBatchSmallThreads = MGR_BATCH_SMALL_THREADS;
+constexpr int kBatchSmallCtas = 1024 / MGR_BATCH_SMALL_THREADS;  // CTAs per SM it is compiled for
 
 template <bool DEC, typename TD, typename TS, typename TW>
-__global__ void __launch_bounds__(kBatchSmallThreads, 2) kb_small(const SmallArgs<TS, TW>* __restrict__ args, int n) {
+__global__ void __launch_bounds__(kBatchSmallThreads, kBatchSmallCtas) kb_small(const SmallArgs<TS, TW>* __restrict__ args, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) SmallArgs<TS, TW> sa;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
@@ -200,6 +218,16 @@ inline int cfg_by(int cfg) { return cfg == 0 ? 14 : 6; }
 
 inline int ctas_per_sm(int cfg) { return cfg == 0 ? 2 : 4; }
 
+// z-chunk length candidates of the autotuner (coarse planes per work item, at most)
+#ifndef MGR_BATCH_CHUNK_MAX
+#define MGR_BATCH_CHUNK_MAX 32
+#endif
+#if MGR_BATCH_CHUNK_MAX > 32
+constexpr int kChunks[] = {8, 16, 32, MGR_BATCH_CHUNK_MAX};
+#else
+constexpr int kChunks[] = {8, 16, 32};
+#endif
+
 // Coarse z planes per work item: at most `chunk`, split evenly over the items
 // (33 planes in chunks of 32 are 17 + 16, not 32 + 1).
 inline int balanced_chunk(int chunk, int mz) {
@@ -238,7 +266,7 @@ struct Builder {
   // Coarse levels taken by the one-CTA phase: the largest ls whose level grid
   // has at most 8192 nodes and whose work arrays fit in kSmallSmemCap bytes
   // (two CTAs per SM).
-  static constexpr size_t kSmallSmemCap = size_t(100) * 1024;
+  static constexpr size_t kSmallSmemCap = size_t(MGR_BATCH_SMALL_SMEM_KB) * 1024;
   int small_levels_of(const mgr_plan* p) const {
     int ls = 0;
     for (int l = 1; l <= p->levels && l <= kSmallMaxLevels; ++l) {
@@ -353,7 +381,10 @@ struct Builder {
   void interp_phase(int d) {
     std::vector<InterpArgs<TS, TW>> descs;
     std::vector<int4> items;
-    constexpr int NW = 8, RPW = 2, BY = NW * RPW;
+#ifndef MGR_BATCH_INTERP_NW
+#define MGR_BATCH_INTERP_NW 2
+#endif
+    constexpr int NW = MGR_BATCH_INTERP_NW, RPW = 2, BY = NW * RPW;
     for (size_t fi = 0; fi < fields.size(); ++fi) {
       const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
@@ -402,7 +433,7 @@ struct Builder {
     ph.fn = reinterpret_cast<const void*>(kb_interp<NW, RPW, TD, TO, TS, TW>);
     ph.block = NW * 32;
     ph.smem = interp_smem_bytes<NW, RPW, TD, TW>();
-    ph.grid = std::min(ph.n_items, num_sms * 2);
+    ph.grid = std::min(ph.n_items, num_sms * level_ctas_per_sm(NW));
     pending.push_back(ph);
   }
 
@@ -584,7 +615,7 @@ struct Builder {
                 : reinterpret_cast<const void*>(kb_small<false, TD, TS, TW>);
     ph.block = kBatchSmallThreads;
     ph.smem = order.front().first;
-    ph.grid = std::min(ph.n_items, num_sms * 2);
+    ph.grid = std::min(ph.n_items, num_sms * kBatchSmallCtas);
     pending.push_back(ph);
   }
 
@@ -863,7 +894,9 @@ bool cache_lookup(const char* path, const std::string& gk, unsigned long long h,
   int cfg = 0, chunk = 0;
   bool found = false;
   while (std::fscanf(f, "%255s %llx %d %d", g, &hh, &cfg, &chunk) == 4) {
-    if (gk == g && hh == h && cfg >= 0 && cfg < kNumCfg && (chunk == 8 || chunk == 16 || chunk == 32)) {
+    bool known = false;
+    for (int c : kChunks) known |= chunk == c;
+    if (gk == g && hh == h && cfg >= 0 && cfg < kNumCfg && known) {
       *out = TileCand{cfg, chunk};  // the last matching line wins
       found = true;
     }
@@ -898,7 +931,7 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
   }
   std::vector<std::pair<double, TileCand>> ranked;
   for (int cfg = 0; cfg < kNumCfg; ++cfg)
-    for (int chunk : {8, 16, 32}) {
+    for (int chunk : kChunks) {
       TileCand c{cfg, chunk};
       ranked.push_back({model_of<TD, TS, TW>(fields, op, c, ctx->num_sms, ctx->smem_optin), c});
     }
