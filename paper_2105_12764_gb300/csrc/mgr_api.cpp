@@ -15,17 +15,31 @@
 namespace mgr {
 
 cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the default limit (48 KB) covers static and dynamic shared memory together
+  constexpr size_t kDefault = 48 * 1024;
+  if (bytes == 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  struct Limit {
+    size_t static_bytes = 0;
+    size_t dynamic = 0;  // the dynamic limit set so far (0: the default)
+    bool known = false;
+  };
   static std::mutex mu;
-  static std::map<std::pair<int, const void*>, size_t> limits;
+  static std::map<std::pair<int, const void*>, Limit> limits;
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = limits[{dev, fn}];
-  if (bytes <= cur) return cudaSuccess;
+  Limit& cur = limits[{dev, fn}];
+  if (!cur.known) {
+    cudaFuncAttributes at{};
+    e = cudaFuncGetAttributes(&at, fn);
+    if (e != cudaSuccess) return e;
+    cur.static_bytes = at.sharedSizeBytes;
+    cur.known = true;
+  }
+  if (bytes + cur.static_bytes <= kDefault || bytes <= cur.dynamic) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-  if (e == cudaSuccess) cur = bytes;
+  if (e == cudaSuccess) cur.dynamic = bytes;
   return e;
 }
 

@@ -15,8 +15,9 @@
 //
 // Autotuning (Sec. III.B: an analytic model ranks the candidate launch
 // shapes, the best few are measured): candidates are the level-pass tile
-// (8 warps x 2 row pairs = 30x14 coarse nodes, or 4 warps x 2 = 30x6) and the
-// z-chunk length (at most 8, 16 or 32 coarse planes, split evenly over a
+// (8 warps x 2 row pairs = 30x14 coarse nodes, 4 warps x 2 = 30x6, or 4 warps
+// in half-warp row groups x 2 = 14x14, for fields whose coarse rows are
+// short) and the z-chunk length (at most 8, 16 or 32 coarse planes, split evenly over a
 // field's items).  The model charges each work item the shared-memory slots
 // it streams (halo and padding included) and takes the longer of the memory
 // time and the longest-processing-time schedule of the items over the
@@ -61,7 +62,7 @@ __device__ __forceinline__ void copy_words(T* dst, const T* src) {
   for (int i = threadIdx.x; i < int(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
 }
 
-template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW>
+template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, int LX = 32>
 __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_level(const LevelArgs<TS, TW>* __restrict__ args,
                                                        const int4* __restrict__ items, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_level(const
     const int4 it = items[i];
     copy_words(&sa, args + it.x);
     __syncthreads();
-    level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW>(sa, it.y, it.z, it.w, smem_raw);
+    level_body<MODE, NW, RPW, STAGES, TI, TD, TS, TW, false, false, false, LX>(sa, it.y, it.z, it.w, smem_raw);
     __syncthreads();
   }
 }
@@ -208,13 +209,17 @@ struct FieldRef {
   char* ws;
 };
 
-// Level-pass tile candidates (NW warps x RPW row pairs); chunk lengths.
+// Level-pass tile candidates (NW warps x RPW row pairs per row group of LX
+// lanes); chunk lengths.
 struct TileCand {
-  int cfg;    // 0: 8 warps x 2 row pairs (30 x 14), 1: 4 warps x 2 (30 x 6)
+  int cfg;    // 0: 8 warps x 2 row pairs (30 x 14), 1: 4 warps x 2 (30 x 6),
+              // 2: 4 warps as 8 half-warp row groups x 2 (14 x 14)
   int chunk;  // coarse z planes per work item
 };
-constexpr int kNumCfg = 2;
-inline int cfg_by(int cfg) { return cfg == 0 ? 14 : 6; }
+constexpr int kNumCfg = 3;
+inline int cfg_bx(int cfg) { return cfg == 2 ? 14 : 30; }
+inline int cfg_by(int cfg) { return cfg == 1 ? 6 : 14; }
+inline const char* cfg_name(int cfg) { return cfg == 0 ? "30x14" : cfg == 1 ? "30x6" : "14x14"; }
 
 inline int ctas_per_sm(int cfg) { return cfg == 0 ? 2 : 4; }
 
@@ -253,7 +258,7 @@ struct Builder {
     int grid;
   };
   std::vector<PendingPhase> pending;
-  std::vector<std::function<void(cudaStream_t)>> copies;  // levels == 0 fields
+  std::vector<std::function<cudaError_t(cudaStream_t)>> copies;  // levels == 0 fields
 
   std::vector<int> small;  // per field: its levels 1..small[f] run in one CTA (kb_small)
   size_t smem_optin;
@@ -312,7 +317,7 @@ struct Builder {
   void level_phase(int d, bool first_dec) {
     std::vector<LevelArgs<TS, TW>> descs;
     std::vector<int4> items;
-    const int BX = 30, BY = cfg_by(cand.cfg);
+    const int BX = cfg_bx(cand.cfg), BY = cfg_by(cand.cfg);
     for (size_t fi = 0; fi < fields.size(); ++fi) {
       const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
@@ -367,11 +372,16 @@ struct Builder {
       ph.fn = reinterpret_cast<const void*>(kb_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>);
       ph.block = C::NW * 32;
       ph.smem = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
-    } else {
+    } else if (cand.cfg == 1) {
       constexpr int ST = LevelCfg<TS>::STAGES;
       ph.fn = reinterpret_cast<const void*>(kb_level<MODE, 4, 2, ST, TI, TD, TS, TW>);
       ph.block = 128;
       ph.smem = level_smem_bytes<4, 2, ST, TI, TS>();
+    } else {
+      constexpr int ST = LevelCfg<TS>::STAGES;
+      ph.fn = reinterpret_cast<const void*>(kb_level<MODE, 4, 2, ST, TI, TD, TS, TW, 16>);
+      ph.block = 128;
+      ph.smem = level_smem_bytes<4, 2, ST, TI, TS, 16>();
     }
     ph.grid = std::min(ph.n_items, num_sms * ctas_per_sm(cand.cfg));
     pending.push_back(ph);
@@ -626,7 +636,7 @@ struct Builder {
       if (fr.p->levels == 0 && fr.in != fr.out) {
         const FieldRef f = fr;
         copies.push_back([f](cudaStream_t st) {
-          cudaMemcpyAsync(f.out, f.in, size_t(f.p->count) * f.p->elem, cudaMemcpyDeviceToDevice, st);
+          return cudaMemcpyAsync(f.out, f.in, size_t(f.p->count) * f.p->elem, cudaMemcpyDeviceToDevice, st);
         });
       }
     }
@@ -660,8 +670,8 @@ struct Builder {
   // the LPT schedule of the items over the persistent CTAs.
   double model_cost(double hbm_bytes_per_us) const {
     double total = 0;
-    const int BY = cfg_by(cand.cfg);
-    const int RR = 2 * (BY + 2), RC = 64;
+    const int BX = cfg_bx(cand.cfg), BY = cfg_by(cand.cfg);
+    const int RR = 2 * (BY + 2), RC = 2 * (BX + 2);
     const int slots = num_sms * ctas_per_sm(cand.cfg);
     const double t_iter_us = (cand.cfg == 0 ? 1.6 : 1.0);
     int D = 0;
@@ -675,7 +685,7 @@ struct Builder {
         if (!tiled(fi, d)) continue;
         const LevelGeom& g = fr.p->geom[L - d];
         const int chunk = balanced_chunk(cand.chunk, g.ax[0].m);
-        const int gx = (g.ax[2].m + 29) / 30, gy = (g.ax[1].m + BY - 1) / BY;
+        const int gx = (g.ax[2].m + BX - 1) / BX, gy = (g.ax[1].m + BY - 1) / BY;
         const int gz = (g.ax[0].m + chunk - 1) / chunk;
         for (int z = 0; z < gz; ++z) {
           const int planes = std::min(chunk, g.ax[0].m - z * chunk) + 1;
@@ -718,8 +728,9 @@ struct BatchExec {
     size_t smem;
   };
   std::vector<L> launches;
-  std::vector<std::function<void(cudaStream_t)>> copies;
+  std::vector<std::function<cudaError_t(cudaStream_t)>> copies;
   cudaGraphExec_t graph = nullptr;
+  mutable std::string failed;  // the launch that failed last, for the tuning report
   ~BatchExec() {
     if (graph) cudaGraphExecDestroy(graph);
     if (dev) cudaFree(dev);
@@ -728,18 +739,31 @@ struct BatchExec {
     static const char* kinds[] = {"level pass", "interpolation", "strided solves", "contiguous solves",
                                   "coarsest copy", "coarse levels in one CTA"};
     NvtxRange op_range("mgr batch: %d phases", int(launches.size()));
-    for (auto& c : copies) c(st);
+    for (auto& c : copies) {
+      const cudaError_t e = c(st);
+      if (e != cudaSuccess) {
+        failed = std::string("copy of a field without levels: ") + cudaGetErrorName(e);
+        return e;
+      }
+    }
     for (const L& l : launches) {
       NvtxRange phase_range("batch phase: %s", kinds[l.kind]);
-      raise_smem_limit(l.fn, l.smem);
-      if (l.kind == 4 || l.kind == 5) {
-        void* args[] = {const_cast<void**>(&l.desc), const_cast<int*>(&l.n)};
-        cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
-        if (e != cudaSuccess) return e;
-      } else {
-        void* args[] = {const_cast<void**>(&l.desc), const_cast<void**>(&l.items), const_cast<int*>(&l.n)};
-        cudaError_t e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
-        if (e != cudaSuccess) return e;
+      cudaError_t e = raise_smem_limit(l.fn, l.smem);
+      if (e == cudaSuccess) {
+        if (l.kind == 4 || l.kind == 5) {
+          void* args[] = {const_cast<void**>(&l.desc), const_cast<int*>(&l.n)};
+          e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
+        } else {
+          void* args[] = {const_cast<void**>(&l.desc), const_cast<void**>(&l.items), const_cast<int*>(&l.n)};
+          e = cudaLaunchKernel(l.fn, l.grid, l.block, args, l.smem, st);
+        }
+      }
+      if (e != cudaSuccess) {
+        char b[192];
+        std::snprintf(b, sizeof(b), "%s (grid %u, block %u, %zu B shared memory, %d items): %s", kinds[l.kind],
+                      l.grid.x, l.block.x, l.smem, l.n, cudaGetErrorName(e));
+        failed = b;
+        return e;
       }
     }
     return cudaGetLastError();
@@ -813,6 +837,7 @@ struct BatchState {
   std::map<std::string, TileCand> tuned;
   std::map<std::string, std::vector<std::pair<TileCand, double>>> tune_log;
   std::map<std::string, bool> from_file;  // decision read from the persisted cache
+  std::map<std::string, std::string> tune_note;  // the launch a failed candidate stopped at
 };
 
 namespace {
@@ -840,23 +865,31 @@ int exec_for(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fields, i
 }
 
 // Time one candidate on the real batch (graph-less, after one warm-up run).
+// A candidate that fails (a launch refused, or any CUDA error while it runs)
+// returns minus its CUDA error code: it is never the fastest, and the tuning
+// report names the error.
 template <typename TD, typename TS, typename TW>
-double time_candidate(mgr_ctx* ctx, const std::vector<FieldRef>& fields, int op, TileCand cand, cudaStream_t st) {
+double time_candidate(mgr_ctx* ctx, const std::vector<FieldRef>& fields, int op, TileCand cand, cudaStream_t st,
+                      std::string* failed) {
   std::unique_ptr<BatchExec> ex;
-  if (make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ctx->smem_optin, ex) != MGR_OK) return 1e30;
+  if (make_exec<TD, TS, TW>(fields, op, cand, ctx->num_sms, ctx->smem_optin, ex) != MGR_OK)
+    return -double(cudaErrorMemoryAllocation);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  ex->enqueue(st);
+  cudaError_t e = ex->enqueue(st);
   cudaEventRecord(a, st);
-  ex->enqueue(st);
+  if (e == cudaSuccess) e = ex->enqueue(st);
   cudaEventRecord(b, st);
-  float ms = 1e30f;
-  if (cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  float ms = 0.f;
+  const cudaError_t es = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = es;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaGetLastError();
-  return ms;
+  if (e != cudaSuccess && failed && !ex->failed.empty()) *failed = ex->failed;
+  return e == cudaSuccess ? double(ms) : -double(e);
 }
 
 // Persisted decisions: the environment variable MGR_AUTOTUNE_CACHE names a
@@ -956,9 +989,11 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
   double best_ms = 1e30;
   std::vector<std::pair<TileCand, double>> log;
   for (const TileCand& c : timed) {
-    const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, c, B.stream);
+    std::string why;
+    const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, c, B.stream, &why);
     log.push_back({c, ms});
-    if (ms < best_ms) {
+    if (!why.empty()) B.tune_note[skey] = why;
+    if (ms >= 0.0 && ms < best_ms) {
       best_ms = ms;
       best = c;
     }
@@ -1175,14 +1210,19 @@ int batch_tuning(mgr_ctx* ctx, char* buf, size_t len) {
       s += "shape[" + std::to_string(kv.first.size()) + " chars]";
       const TileCand c = B->tuned[kv.first];
       char line[128];
-      std::snprintf(line, sizeof(line), " chosen tile=%s chunk=%d;%s", c.cfg == 0 ? "30x14" : "30x6", c.chunk,
+      std::snprintf(line, sizeof(line), " chosen tile=%s chunk=%d;%s", cfg_name(c.cfg), c.chunk,
                     B->from_file.count(kv.first) ? " (from the persisted cache)" : "");
       s += line;
       for (auto& m : kv.second) {
-        std::snprintf(line, sizeof(line), " [%s/%d: %.3f ms]", m.first.cfg == 0 ? "30x14" : "30x6", m.first.chunk,
-                      m.second);
+        if (m.second >= 0.0)
+          std::snprintf(line, sizeof(line), " [%s/%d: %.3f ms]", cfg_name(m.first.cfg), m.first.chunk, m.second);
+        else
+          std::snprintf(line, sizeof(line), " [%s/%d: failed, %s]", cfg_name(m.first.cfg), m.first.chunk,
+                        cudaGetErrorName(cudaError_t(int(-m.second))));
         s += line;
       }
+      auto nt = B->tune_note.find(kv.first);
+      if (nt != B->tune_note.end()) s += " failed at: " + nt->second;
       s += "\n";
     }
   }

@@ -206,8 +206,9 @@ bool fault_injected(const char* what);
 // Raise the dynamic shared-memory limit of kernel `fn` on the current device
 // to at least `bytes`.  The limit only ever grows: a launch captured into a
 // graph (or issued from another thread) with a larger request than the
-// current one is never left above a lowered limit.  Requests up to the 48 KB
-// that every kernel may use without the attribute need no call.
+// current one is never left above a lowered limit.  Requests that fit, with
+// the kernel's static shared memory, in the 48 KB every kernel may use
+// without the attribute need no call.
 cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 template <typename F>
 inline cudaError_t raise_smem_limit(F* fn, size_t bytes) {

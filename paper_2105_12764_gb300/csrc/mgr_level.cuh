@@ -8,11 +8,15 @@
 // fine-in-z plane p(t)-1 between p(t-1) and p(t).
 //
 // Thread mapping (fixed for the CTA's lifetime, so every per-row and
-// per-column weight and address is computed once): lane l owns the fine
-// column pair (rx0 + 2l, rx0 + 2l + 1) of the region, warp w owns RPW fine
-// row pairs.  The region starts on a coarse node, so the first node of every
-// pair is coarse and the second is the fine node between two coarse ones
-// (or, at the end of an axis whose length is even, the last coarse node).
+// per-column weight and address is computed once): the CTA's threads form
+// row groups of LX lanes (a whole warp, LX = 32, or half of one, LX = 16:
+// a tile 14 coarse nodes wide, for fields whose coarse rows are short);
+// lane l of a group owns the fine column pair (rx0 + 2l, rx0 + 2l + 1) of
+// the region, group w owns RPW fine row pairs.  Below, "lane" and "warp"
+// are a thread's lane in its group and its group.  The region starts on a
+// coarse node, so the first node of every pair is coarse and the second is
+// the fine node between two coarse ones (or, at the end of an axis whose
+// length is even, the last coarse node).
 //
 // Coefficients (Sec. II.A.1), separable and in the paper's FMA form
 // (Table "fma"): on a coarse-z plane the x interpolant of a coarse row uses
@@ -43,14 +47,20 @@
 // code * q_l; q_l is the bin width of the level's class.
 #pragma once
 
-template <int NW, int RPW>
+template <int NW, int RPW, int LX = 32>
 struct LevelTile {
+  static_assert(LX == 32 || LX == 16, "row groups of a warp or half a warp");
   static constexpr int NT = NW * 32;
-  static constexpr int BX = 30;            // coarse x outputs per CTA
-  static constexpr int BY = NW * RPW - 2;  // coarse y outputs per CTA
-  static constexpr int RC = 64;            // fine column slots (region width <= 2*BX+3 = 63)
-  static constexpr int RR = 2 * NW * RPW;  // fine row slots (region height <= 2*BY+3 = RR-1)
+  static constexpr int NG = NT / LX;       // row groups
+  static constexpr int BX = LX - 2;        // coarse x outputs per CTA
+  static constexpr int BY = NG * RPW - 2;  // coarse y outputs per CTA
+  static constexpr int RC = 2 * LX;        // fine column slots (region width <= 2*BX+3 = RC-1)
+  static constexpr int RR = 2 * NG * RPW;  // fine row slots (region height <= 2*BY+3 = RR-1)
   static constexpr int CP = RC + 2;        // c row pitch: even, so column pairs stay 8/16-byte aligned
+  // x-stencil result row pitch: with half-warp groups the two halves of a warp
+  // work 2*RPW rows apart, and a pitch of 4 (mod 8) words puts them in
+  // different banks
+  static constexpr int GP = LX == 32 ? 32 : LX + 4;
 };
 
 // Tile configuration of the level pass per stencil type: 8 warps with two
@@ -203,11 +213,12 @@ constexpr bool weights_in_smem() {
   return sizeof(TS) == 8;
 }
 
-template <int NW, int RPW, int STAGES, typename TI, typename TS>
+template <int NW, int RPW, int STAGES, typename TI, typename TS, int LX = 32>
 constexpr size_t level_smem_bytes() {
-  using G = LevelTile<NW, RPW>;
+  using G = LevelTile<NW, RPW, LX>;
   return sizeof(TI) * STAGES * 2 * G::RR * G::RC +
-         sizeof(TS) * (2 * G::RR * G::CP + 2 * G::RR * 32 + 5 * 32 + 5 * NW * RPW + (sizeof(TS) == 8 ? NW * G::RC : 0));
+         sizeof(TS) * (2 * G::RR * G::CP + 2 * G::RR * G::GP + 5 * LX + 5 * G::NG * RPW +
+                       (sizeof(TS) == 8 ? G::NG * G::RC : 0));
 }
 
 // Copy the element pair (c0, c0+1) of one row into shared memory: one
@@ -253,23 +264,24 @@ __device__ __forceinline__ void store_pair(T* p0, T* p1, T a0, T a1, bool w0, bo
 // QZ (with PK): those coefficients are int32 codes (TD = int in MODE 0, TI =
 // int in MODE 1).
 // AF: honour `all_fine` (the 4D form's time slices; a runtime flag read once).
+// LX: lanes per row group (32 or 16).
 template <int MODE, int NW, int RPW, int STAGES, typename TI, typename TD, typename TS, typename TW, bool PK = false,
-          bool QZ = false, bool AF = false>
+          bool QZ = false, bool AF = false, int LX = 32>
 __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, int by, int bz,
                                            unsigned char* smem_raw) {
-  using G = LevelTile<NW, RPW>;
+  using G = LevelTile<NW, RPW, LX>;
   using TS2 = typename Pair<TS>::type;
   using TI2 = typename Pair<TI>::type;
-  constexpr int RR = G::RR, RC = G::RC, CP = G::CP;
+  constexpr int RR = G::RR, RC = G::RC, CP = G::CP, GP = G::GP, NG = G::NG;
   constexpr unsigned FULL = 0xffffffffu;
   TI* stage = reinterpret_cast<TI*>(smem_raw);                                       // [STAGES][2][RR][RC]
   TS* cbuf = reinterpret_cast<TS*>(smem_raw + sizeof(TI) * STAGES * 2 * RR * RC);  // [2][RR][CP]
-  TS* gxb = cbuf + 2 * RR * CP;                                                     // [2][RR][32]
-  TS* kxs = gxb + 2 * RR * 32;                                                      // [5][32]
-  TS* kys = kxs + 5 * 32;                                                           // [5][NW*RPW]
-  TS* xch = kys + 5 * NW * RPW;  // [NW][RC] FP64 only: x interpolants of each warp's first coarse row
+  TS* gxb = cbuf + 2 * RR * CP;                                                     // [2][RR][GP]
+  TS* kxs = gxb + 2 * RR * GP;                                                      // [5][LX]
+  TS* kys = kxs + 5 * LX;                                                           // [5][NG*RPW]
+  TS* xch = kys + 5 * NG * RPW;  // [NG][RC] FP64 only: x interpolants of each group's first coarse row
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x % LX, warp = threadIdx.x / LX;  // lane in the row group, row group
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
   const int mz = a.m[0], my = a.m[1], mx = a.m[2];
   const int qx0 = bx * G::BX, qx1 = min(qx0 + G::BX, mx);
@@ -355,7 +367,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   for (int o = 0; o < 5; ++o) {
     const TS kw = a.k[2][5 * qxo + o];
     if constexpr (weights_in_smem<TS>()) {
-      if (warp == 0) kxs[o * 32 + lane] = kw;
+      if (warp == 0) kxs[o * LX + lane] = kw;
     } else {
       kxr[o] = kw;
     }
@@ -363,7 +375,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     if (j >= 0 && j < nx) kxm |= 1u << o;
   }
   auto kx = [&](int o) -> TS {
-    if constexpr (weights_in_smem<TS>()) return kxs[o * 32 + lane];
+    if constexpr (weights_in_smem<TS>()) return kxs[o * LX + lane];
     else return kxr[o];
   };
   // interior column: taps px +- 1 fine, px and px +- 2 coarse, even slot
@@ -376,12 +388,12 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   constexpr bool BF = sizeof(TS) == 4;
   // FP32 nodal decomposition (RS): the coefficients go out after the
   // coefficient phase, row by row from the shared tile, each lane storing
-  // output columns ox0 + lane and ox0 + 32 + lane (consecutive lanes,
+  // output columns ox0 + lane and ox0 + LX + lane (consecutive lanes,
   // consecutive addresses): the coefficient phase then keeps no output
   // addresses or values live (it is short of registers).  All-coarse nodes
   // get 0 there, a placeholder a coarser level overwrites.
   constexpr bool RS = BF && !PK && MODE == 0;
-  const int oc0 = ox0 + lane, oc1 = oc0 + 32;
+  const int oc0 = ox0 + lane, oc1 = oc0 + LX;
   const bool rs0 = oc0 < ox1, rs1 = oc1 < ox1;
   const int ro0 = int(fmap(min(oc0, nx - 1), a.s[2], a.N[2])), ro1 = int(fmap(min(oc1, nx - 1), a.s[2], a.N[2]));
   const int rsl0 = oc0 - rx0, rsl1 = oc1 - rx0;
@@ -420,7 +432,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     for (int o = 0; o < 5; ++o) {
       const TS kw = a.k[1][5 * qy + o];
       if constexpr (weights_in_smem<TS>()) {
-        if (lane == 0) kys[o * (NW * RPW) + warp * RPW + k] = kw;
+        if (lane == 0) kys[o * (NG * RPW) + warp * RPW + k] = kw;
       } else {
         kyr[k][o] = kw;
       }
@@ -432,7 +444,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     if (warp * RPW + k >= nby) kym[k] = 0;
   }
   auto ky = [&](int k, int o) -> TS {
-    if constexpr (weights_in_smem<TS>()) return kys[o * (NW * RPW) + warp * RPW + k];
+    if constexpr (weights_in_smem<TS>()) return kys[o * (NG * RPW) + warp * RPW + k];
     else return kyr[k][o];
   };
 #ifdef MGR_DEBUG_BOUNDS
@@ -560,8 +572,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     TS v12[RPW];
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
-      const TS v02 = __shfl_down_sync(FULL, vc[k][0], 1);
-      v12[k] = __shfl_down_sync(FULL, vc[k][2], 1);
+      const TS v02 = __shfl_down_sync(FULL, vc[k][0], 1, LX);
+      v12[k] = __shfl_down_sync(FULL, vc[k][2], 1, LX);
       if (MODE == 0) {
         In[k][0] = vc[k][0];
         In[k][1] = fx1 ? wax1 * vc[k][0] + wbx1 * v02 : vc[k][1];
@@ -576,10 +588,13 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     if constexpr (!BF) {
       if (MODE == 0) *reinterpret_cast<TS2*>(xch + warp * RC + cx0) = TS2{In[0][0], In[0][1]};
       __syncthreads();
-    } else if (MODE == 0 && warp + 1 < NW) {
-      const TI2 pn = *reinterpret_cast<const TI2*>(sc + 2 * (warp + 1) * RPW * RC + cx0);
+    } else if (MODE == 0 && (LX < 32 || warp + 1 < NG)) {
+      // (half-warp groups: both halves of a warp take this branch, so that the
+      // shuffle below runs on every lane; the last group's result is unused)
+      const int wn = LX < 32 ? min(warp + 1, NG - 1) : warp + 1;
+      const TI2 pn = *reinterpret_cast<const TI2*>(sc + 2 * wn * RPW * RC + cx0);
       const TS vn0 = cval(pn.x), vn1 = cval(pn.y);
-      const TS vn2 = __shfl_down_sync(FULL, vn0, 1);
+      const TS vn2 = __shfl_down_sync(FULL, vn0, 1, LX);
       nxt0 = vn0;
       nxt1 = fx1 ? wax1 * vn0 + wbx1 * vn2 : vn1;
     }
@@ -599,7 +614,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         if (k + 1 < RPW) {
           n0 = In[k + 1 < RPW ? k + 1 : k][0];
           n1 = In[k + 1 < RPW ? k + 1 : k][1];
-        } else if (warp + 1 < NW) {
+        } else if (warp + 1 < NG) {
           if constexpr (BF) {
             n0 = nxt0;
             n1 = nxt1;
@@ -752,8 +767,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           const TS2 a23 = *reinterpret_cast<const TS2*>(row + 2);
           const TS2 b01 = *reinterpret_cast<const TS2*>(rf);
           const TS2 b23 = *reinterpret_cast<const TS2*>(rf + 2);
-          gxb[r * 32 + lane] = kx(0) * a01.x + kx(1) * a01.y + kx(2) * a23.x + kx(3) * a23.y + kx(4) * row[4];
-          gxb[RR * 32 + r * 32 + lane] = kx(0) * b01.x + kx(1) * b01.y + kx(2) * b23.x + kx(3) * b23.y + kx(4) * rf[4];
+          gxb[r * GP + lane] = kx(0) * a01.x + kx(1) * a01.y + kx(2) * a23.x + kx(3) * a23.y + kx(4) * row[4];
+          gxb[RR * GP + r * GP + lane] = kx(0) * b01.x + kx(1) * b01.y + kx(2) * b23.x + kx(3) * b23.y + kx(4) * rf[4];
         }
       }
     } else if (BF && kxo) {
@@ -772,8 +787,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
             g += kx(o) * row[j];
             gf += kx(o) * rf[j];
           }
-          gxb[r * 32 + lane] = g;
-          gxb[RR * 32 + r * 32 + lane] = gf;
+          gxb[r * GP + lane] = g;
+          gxb[RR * GP + r * GP + lane] = gf;
         }
       }
     } else if (!BF && kxo) {
@@ -809,8 +824,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
                 if (hf) gf += kx(o) * cf[r * CP + dx - 2 + o];
               }
           }
-          gxb[r * 32 + lane] = g;
-          if (hf) gxb[RR * 32 + r * 32 + lane] = gf;
+          gxb[r * GP + lane] = g;
+          if (hf) gxb[RR * GP + r * GP + lane] = gf;
         }
       }
     }
@@ -840,16 +855,18 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         const TS* gcol = gxb + lane;
         TS gc = TS(0), gf = TS(0);
         if (kym[k] == 31u) {
-          const TS* g0 = gcol + (dyo[k] - 2) * 32;
-          gc = ky(k, 0) * g0[0] + ky(k, 1) * g0[32] + ky(k, 2) * g0[64] + ky(k, 3) * g0[96] + ky(k, 4) * g0[128];
-          const TS* f0 = g0 + RR * 32;
-          gf = ky(k, 0) * f0[0] + ky(k, 1) * f0[32] + ky(k, 2) * f0[64] + ky(k, 3) * f0[96] + ky(k, 4) * f0[128];
+          const TS* g0 = gcol + (dyo[k] - 2) * GP;
+          gc = ky(k, 0) * g0[0] + ky(k, 1) * g0[GP] + ky(k, 2) * g0[2 * GP] + ky(k, 3) * g0[3 * GP] +
+               ky(k, 4) * g0[4 * GP];
+          const TS* f0 = g0 + RR * GP;
+          gf = ky(k, 0) * f0[0] + ky(k, 1) * f0[GP] + ky(k, 2) * f0[2 * GP] + ky(k, 3) * f0[3 * GP] +
+               ky(k, 4) * f0[4 * GP];
         } else {
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
             const int rr = min(max(dyo[k] + o - 2, 0), RR - 1);
-            gc += ky(k, o) * gcol[rr * 32];
-            gf += ky(k, o) * gcol[RR * 32 + rr * 32];
+            gc += ky(k, o) * gcol[rr * GP];
+            gf += ky(k, o) * gcol[RR * GP + rr * GP];
           }
         }
         acc0[k] += wzc[0] * gc;
@@ -861,21 +878,21 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           LVL_F(int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
       } else if (j < nby && kxo) {
         TS gc = TS(0), gf = TS(0);
-        const TS* gcol = gxb + (dyo[k] - 2) * 32 + lane;
+        const TS* gcol = gxb + (dyo[k] - 2) * GP + lane;
         if (kym[k] == 31u) {  // interior row: all five taps inside the grid
-          gc = ky(k, 0) * gcol[0] + ky(k, 1) * gcol[32] + ky(k, 2) * gcol[64] + ky(k, 3) * gcol[96] +
-               ky(k, 4) * gcol[128];
+          gc = ky(k, 0) * gcol[0] + ky(k, 1) * gcol[GP] + ky(k, 2) * gcol[2 * GP] + ky(k, 3) * gcol[3 * GP] +
+               ky(k, 4) * gcol[4 * GP];
           if (hf) {
-            const TS* fcol = gcol + RR * 32;
-            gf = ky(k, 0) * fcol[0] + ky(k, 1) * fcol[32] + ky(k, 2) * fcol[64] + ky(k, 3) * fcol[96] +
-                 ky(k, 4) * fcol[128];
+            const TS* fcol = gcol + RR * GP;
+            gf = ky(k, 0) * fcol[0] + ky(k, 1) * fcol[GP] + ky(k, 2) * fcol[2 * GP] + ky(k, 3) * fcol[3 * GP] +
+                 ky(k, 4) * fcol[4 * GP];
           }
         } else {
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
             if (kym[k] & (1u << o)) {
-              gc += ky(k, o) * gxb[(dyo[k] + o - 2) * 32 + lane];
-              if (hf) gf += ky(k, o) * gxb[RR * 32 + (dyo[k] + o - 2) * 32 + lane];
+              gc += ky(k, o) * gxb[(dyo[k] + o - 2) * GP + lane];
+              if (hf) gf += ky(k, o) * gxb[RR * GP + (dyo[k] + o - 2) * GP + lane];
             }
           }
         }

@@ -135,3 +135,52 @@ def test_autotune_decision_persists_across_contexts(tmp_path, monkeypatch):
         c.close()
     for a, b in zip(*results):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype,tol", [(mgr.MGR_F32, 1e-5), (mgr.MGR_F64, 1e-12)])
+def test_every_tile_shape_matches_oracle(tmp_path, monkeypatch, dtype, tol):
+    """Each level-pass tile shape of the batched form (30x14, 30x6, and 14x14 in
+    half-warp row groups) and two chunk lengths, forced through the persisted
+    decision file: the first context records its decisions, each later one
+    reads an edited file and runs that shape, and every result equals the
+    oracle (decomposition) and the input (recomposition)."""
+    path = tmp_path / "autotune.txt"
+    monkeypatch.setenv("MGR_AUTOTUNE_CACHE", str(path))
+    rng = np.random.default_rng(33 + dtype)
+    fields = make_fields(rng, 12, dtype)
+    # coarse rows shorter and longer than one tile, ragged in every axis
+    extra = [(97, 45, 70), (33, 18, 129), (9, 65, 31)]
+    for shape in extra:
+        u = rng.standard_normal(shape)
+        fields.append((u.astype(np.float32) if dtype == mgr.MGR_F32 else u, [stretched(s) for s in shape]))
+    refs = [oracle.decompose(u.astype(np.float64), coords) for u, coords in fields]
+
+    def run():
+        c = mgr.Context(0)
+        plans = [mgr.Plan(c, u.shape, coords, -1, dtype) for u, coords in fields]
+        ins = [torch.from_numpy(u).cuda() for u, _ in fields]
+        outs = [torch.full_like(x, float("nan")) for x in ins]
+        backs = [torch.full_like(x, float("nan")) for x in ins]
+        t = c.batch_submit([(mgr.MGR_OP_DECOMPOSE, p, a, b) for p, a, b in zip(plans, ins, outs)])
+        assert c.batch_poll(t, -1)[0] == mgr.MGR_OK
+        t = c.batch_submit([(mgr.MGR_OP_RECOMPOSE, p, b, d) for p, b, d in zip(plans, outs, backs)])
+        assert c.batch_poll(t, -1)[0] == mgr.MGR_OK
+        torch.cuda.synchronize()
+        report = c.batch_tuning()
+        res = [(o.cpu().numpy(), r.cpu().numpy()) for o, r in zip(outs, backs)]
+        for p in plans:
+            p.close()
+        c.close()
+        return report, res
+
+    run()  # records the two decisions (decomposition, recomposition)
+    recorded = [ln.split() for ln in path.read_text().split("\n") if ln.strip()]
+    assert len(recorded) == 2
+    for cfg, name in enumerate(["30x14", "30x6", "14x14"]):
+        for chunk in (8, 16):
+            path.write_text("".join(f"{g} {h} {cfg} {chunk}\n" for g, h, _, _ in recorded))
+            report, res = run()
+            assert f"chosen tile={name} chunk={chunk}" in report and "persisted cache" in report, report
+            for (u, _), ref, (got, back) in zip(fields, refs, res):
+                assert rel_linf(got, ref) <= tol, (name, chunk, u.shape)
+                assert rel_linf(back, u) <= max(tol, 1e-13), (name, chunk, u.shape)
