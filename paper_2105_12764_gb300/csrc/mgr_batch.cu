@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_level(const
   }
 }
 
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW>
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, int LX = 32>
 __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_interp(const InterpArgs<TS, TW>* __restrict__ args,
                                                         const int4* __restrict__ items, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) kb_interp(cons
     const int4 it = items[i];
     copy_words(&sa, args + it.x);
     __syncthreads();
-    interp_body<NW, RPW, TD, TO, TS, TW>(sa, it.y, it.z, it.w, smem_raw);
+    interp_body<NW, RPW, TD, TO, TS, TW, false, false, LX>(sa, it.y, it.z, it.w, smem_raw);
     __syncthreads();
   }
 }
@@ -227,6 +227,7 @@ inline int ctas_per_sm(int cfg) { return cfg == 0 ? 2 : 4; }
 #ifndef MGR_BATCH_CHUNK_MAX
 #define MGR_BATCH_CHUNK_MAX 32
 #endif
+static_assert(MGR_BATCH_CHUNK_MAX <= kLevelMaxChunk, "level-pass chunks are at most kLevelMaxChunk planes");
 #if MGR_BATCH_CHUNK_MAX > 32
 constexpr int kChunks[] = {8, 16, 32, MGR_BATCH_CHUNK_MAX};
 #else
@@ -392,9 +393,14 @@ struct Builder {
     std::vector<InterpArgs<TS, TW>> descs;
     std::vector<int4> items;
 #ifndef MGR_BATCH_INTERP_NW
-#define MGR_BATCH_INTERP_NW 2
+#define MGR_BATCH_INTERP_NW 1
 #endif
-    constexpr int NW = MGR_BATCH_INTERP_NW, RPW = 2, BY = NW * RPW;
+#ifndef MGR_BATCH_INTERP_LX
+#define MGR_BATCH_INTERP_LX 16
+#endif
+    // tiles of LX x BY coarse nodes: half-warp row groups fit the short coarse
+    // rows of the batch's fields better than whole warps
+    constexpr int NW = MGR_BATCH_INTERP_NW, RPW = 2, LX = MGR_BATCH_INTERP_LX, BY = NW * 32 / LX * RPW;
     for (size_t fi = 0; fi < fields.size(); ++fi) {
       const FieldRef& fr = fields[fi];
       const int L = fr.p->levels;
@@ -429,7 +435,7 @@ struct Builder {
       a.qz_chunk = balanced_chunk(cand.chunk, g.ax[0].m);
       const int di = int(descs.size());
       descs.push_back(a);
-      const int gx = (a.m[2] + 31) / 32, gy = (a.m[1] + BY - 1) / BY, gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
+      const int gx = (a.m[2] + LX - 1) / LX, gy = (a.m[1] + BY - 1) / BY, gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
       for (int z = 0; z < gz; ++z)
         for (int y = 0; y < gy; ++y)
           for (int x = 0; x < gx; ++x) items.push_back(make_int4(di, x, y, z));
@@ -440,9 +446,9 @@ struct Builder {
     ph.desc_off = blob.put(descs.data(), descs.size() * sizeof(descs[0]));
     ph.items_off = blob.put(items.data(), items.size() * sizeof(int4));
     ph.n_items = int(items.size());
-    ph.fn = reinterpret_cast<const void*>(kb_interp<NW, RPW, TD, TO, TS, TW>);
+    ph.fn = reinterpret_cast<const void*>(kb_interp<NW, RPW, TD, TO, TS, TW, LX>);
     ph.block = NW * 32;
-    ph.smem = interp_smem_bytes<NW, RPW, TD, TW>();
+    ph.smem = interp_smem_bytes<NW, RPW, TD, TW, LX>();
     ph.grid = std::min(ph.n_items, num_sms * level_ctas_per_sm(NW));
     pending.push_back(ph);
   }

@@ -79,13 +79,15 @@ LevelArgs<TS, TW> level_args(const mgr_plan* p, int l) {
 // Number of z chunks for `tiles` xy tiles and mz coarse planes: minimise
 // waves x planes streamed per CTA (each chunk also streams ~1.5 halo planes).
 // Chunks may be a single plane: on small levels the plane loop's latency, not
-// the halo's extra work, bounds the pass, so the more CTAs the better.
-inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_sm) {
+// the halo's extra work, bounds the pass, so the more CTAs the better.  Chunks
+// are at most max_len planes long (the level pass tabulates its planes).
+inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_sm, int max_len = 1 << 30) {
   const int64_t slots = int64_t(p->ctx->num_sms) * ctas_per_sm;
-  int best = 1;
+  const int cmin = std::max(1, (mz + max_len - 1) / max_len);
+  int best = cmin;
   double best_cost = 1e300;
-  const int cmax = std::max(1, std::min(mz, 64));
-  for (int c = 1; c <= cmax; ++c) {
+  const int cmax = std::max(cmin, std::min(mz, 64));
+  for (int c = cmin; c <= cmax; ++c) {
     const int len = (mz + c - 1) / c;
     const int cc = (mz + len - 1) / len;
     const int64_t waves = (tiles * cc + slots - 1) / slots;
@@ -103,7 +105,7 @@ dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
   using C = LevelCfg<TS>;
   using G = LevelTile<C::NW, C::RPW>;
   const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], level_ctas_per_sm(C::NW));
+  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], level_ctas_per_sm(C::NW), kLevelMaxChunk);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   const int gz = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   return dim3(gx, gy, gz);

@@ -213,12 +213,30 @@ constexpr bool weights_in_smem() {
   return sizeof(TS) == 8;
 }
 
+// Plane pairs a level-pass CTA streams at most (its z chunk plus the halo
+// planes before it): the per-plane-pair constants are tabulated once per CTA
+// in shared memory, so the hosts cap the chunk length at kLevelMaxChunk.
+constexpr int kLevelPlanes = 64;
+constexpr int kLevelMaxChunk = kLevelPlanes - 2;
+
+// Byte offset of the plane table in the level pass's shared memory (after the
+// stage buffers, coefficient tiles, x-stencil results and weights).
+template <int NW, int RPW, int STAGES, typename TI, typename TS, int LX = 32>
+constexpr size_t level_table_offset() {
+  using G = LevelTile<NW, RPW, LX>;
+  return (sizeof(TI) * STAGES * 2 * G::RR * G::RC +
+          sizeof(TS) * (2 * G::RR * G::CP + 2 * G::RR * G::GP + 5 * LX + 5 * G::NG * RPW +
+                        (sizeof(TS) == 8 ? G::NG * G::RC : 0)) +
+          15) / 16 * 16;
+}
+// per plane pair: four plane offsets (int64), eight weights (TS), a flag (int)
+template <typename TS>
+constexpr size_t level_table_bytes() {
+  return kLevelPlanes * (4 * sizeof(int64_t) + 8 * sizeof(TS) + sizeof(int));
+}
 template <int NW, int RPW, int STAGES, typename TI, typename TS, int LX = 32>
 constexpr size_t level_smem_bytes() {
-  using G = LevelTile<NW, RPW, LX>;
-  return sizeof(TI) * STAGES * 2 * G::RR * G::RC +
-         sizeof(TS) * (2 * G::RR * G::CP + 2 * G::RR * G::GP + 5 * LX + 5 * G::NG * RPW +
-                       (sizeof(TS) == 8 ? G::NG * G::RC : 0));
+  return level_table_offset<NW, RPW, STAGES, TI, TS, LX>() + level_table_bytes<TS>();
 }
 
 // Copy the element pair (c0, c0+1) of one row into shared memory: one
@@ -280,6 +298,11 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
   TS* kxs = gxb + 2 * RR * GP;                                                      // [5][LX]
   TS* kys = kxs + 5 * LX;                                                           // [5][NG*RPW]
   TS* xch = kys + 5 * NG * RPW;  // [NG][RC] FP64 only: x interpolants of each group's first coarse row
+  // plane table (kLevelPlanes entries): offsets of the input's coarse and fine
+  // planes and of the output's; weights wzc[3], wzf[2], za, zb; has-fine flag
+  int64_t* ptab = reinterpret_cast<int64_t*>(smem_raw + level_table_offset<NW, RPW, STAGES, TI, TS, LX>());
+  TS* pwt = reinterpret_cast<TS*>(ptab + 4 * kLevelPlanes);
+  int* pfl = reinterpret_cast<int*>(pwt + 8 * kLevelPlanes);
 
   const int lane = threadIdx.x % LX, warp = threadIdx.x / LX;  // lane in the row group, row group
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
@@ -463,15 +486,50 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       (void)MGR_IN(dyo[k] + 2, RR, kDbgLevelTile);
     }
 #endif
-  __syncthreads();  // stencil weights staged
-
   auto iplane = [&](int g) -> int64_t {
     if (PK && MODE == 1) return int64_t(g) * a.in_sz - int64_t(cidx(g)) * a.c_sz;
     return a.in_full ? fmap(g, a.s[0], a.N[0]) * a.in_sz : int64_t(g) * a.in_sz;
   };
-  // zc: gz is a coarse plane (a packed class then holds only its fine nodes)
-  auto load_plane = [&](TI* sb, int gz, bool zc) {
-    const TI* base = in + iplane(gz);
+  auto yplane = [&](int g) -> int64_t {
+    return PK ? int64_t(g) * a.y_sz - int64_t(cidx(g)) * a.c_sz : fmap(g, a.s[0], a.N[0]) * a.y_sz;
+  };
+  // ---- plane table, computed once by the CTA (every warp would otherwise
+  // recompute these on each plane pair): plane pair t -- the coarse plane p(t)
+  // and, when a fine plane lies between p(t-1) and p(t), that fine plane -- is
+  // entry t - t_start
+  (void)MGR_IN(t_end - t_start, kLevelPlanes, kDbgLevelTile);
+  for (int e = threadIdx.x; e <= t_end - t_start && e < kLevelPlanes; e += G::NT) {
+    const int t = t_start + e;
+    const int Pc = pidx(t, nz), Pf = Pc - 1;
+    const bool hf = t > t_start && Pc - pidx(t - 1, nz) == 2;
+    ptab[4 * e + 0] = iplane(Pc);
+    ptab[4 * e + 1] = hf ? iplane(Pf) : 0;
+    ptab[4 * e + 2] = yplane(Pc);
+    ptab[4 * e + 3] = yplane(max(Pf, 0));
+    // z stencil weights of both planes for the coarse planes t-1, t, t+1
+    TS* w = pwt + 8 * e;
+#pragma unroll
+    for (int dq = -1; dq <= 1; ++dq) {
+      const int q = t + dq;
+      const bool qv = q >= 0 && q < mz;
+      const int pq = qv ? pidx(q, nz) : 0;
+      const int oc = Pc - pq;
+      w[dq + 1] = (qv && oc >= -2 && oc <= 2) ? a.k[0][5 * q + oc + 2] : TS(0);
+      if (dq < 1) {
+        const int of = Pf - pq;
+        w[dq + 4] = (hf && qv && of >= -2 && of <= 2) ? a.k[0][5 * q + of + 2] : TS(0);
+      }
+    }
+    // z interpolation weights of the fine plane (decomposition)
+    w[6] = (MODE == 0 && hf) ? a.wa[0][Pf] : TS(0);
+    w[7] = (MODE == 0 && hf) ? a.wb[0][Pf] : TS(0);
+    pfl[e] = hf ? 1 : 0;
+  }
+  __syncthreads();  // stencil weights and plane table staged
+  // poff: the plane's offset (plane table); zc: it is a coarse plane (a packed
+  // class then holds only its fine nodes)
+  auto load_plane = [&](TI* sb, int64_t poff, bool zc) {
+    const TI* base = in + poff;
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       TI* d0 = sb + 2 * (warp * RPW + k) * RC + cx0;
@@ -510,14 +568,15 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       }
     }
   };
-  auto has_fine = [&](int t) { return t > t_start && (pidx(t, nz) - pidx(t - 1, nz) == 2); };
   static_assert(STAGES == 1 || STAGES == 2, "one or two stage buffers");
   // stage buffer of plane pair t (two in rotation, or one)
   auto stage_of = [&](int t) { return stage + ((STAGES == 2) ? ((t - t_start) & 1) * 2 * RR * RC : 0); };
   auto issue = [&](int t) {
     TI* sb = stage_of(t);
-    load_plane(sb, pidx(t, nz), true);
-    if (has_fine(t)) load_plane(sb + RR * RC, pidx(t, nz) - 1, false);
+    const int e = t - t_start;
+    const longlong2 off = *reinterpret_cast<const longlong2*>(ptab + 4 * e);
+    load_plane(sb, off.x, true);
+    if (pfl[e]) load_plane(sb + RR * RC, off.y, false);
     cp_commit();
   };
 
@@ -547,9 +606,8 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     __syncthreads();
     const TI* sc = stage_of(t);
     const TI* sf = sc + RR * RC;
-    const int Pc = pidx(t, nz);
-    const bool hf = has_fine(t);
-    const int Pf = Pc - 1;
+    const int te = t - t_start;
+    const bool hf = pfl[te] != 0;
     const bool own_c = (t >= qz0) && (t < qz1);
     const bool own_f = hf && (t > qz0) && (t <= qz1);
 
@@ -602,9 +660,9 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     // ---- coefficients of both planes -> shared memory and the nodal output
     TS* cc = cbuf;
     TS* cf = cbuf + RR * CP;
-    TD* yzc = yout + (PK ? int64_t(Pc) * a.y_sz - int64_t(cidx(Pc)) * a.c_sz : fmap(Pc, a.s[0], a.N[0]) * a.y_sz);
-    TD* yzf = yout + (PK ? int64_t(max(Pf, 0)) * a.y_sz - int64_t(cidx(max(Pf, 0))) * a.c_sz
-                         : fmap(max(Pf, 0), a.s[0], a.N[0]) * a.y_sz);
+    const longlong2 yoff = *reinterpret_cast<const longlong2*>(ptab + 4 * te + 2);
+    TD* yzc = yout + yoff.x;
+    TD* yzf = yout + yoff.y;
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int r0 = 2 * (warp * RPW + k);
@@ -699,7 +757,7 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         }
         TS d[4];
         if (MODE == 0) {
-          const TS za = a.wa[0][Pf], zb = a.wb[0][Pf];
+          const TS za = pwt[8 * te + 6], zb = pwt[8 * te + 7];
 #pragma unroll
           for (int e = 0; e < 4; ++e) d[e] = vf[e] - za * Ip[k][e] - zb * In[k][e];
         } else {
@@ -832,20 +890,12 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     __syncthreads();
 
     // ---- y stencil and z accumulation for this thread's outputs
-    // z weights of the two planes for coarse planes t-1, t, t+1 (uniform)
+    // z weights of the two planes for coarse planes t-1, t, t+1 (plane table)
     TS wzc[3], wzf[2];
 #pragma unroll
-    for (int dq = -1; dq <= 1; ++dq) {
-      const int q = t + dq;
-      const bool qv = q >= 0 && q < mz;
-      const int pq = qv ? pidx(q, nz) : 0;
-      const int oc = Pc - pq;
-      wzc[dq + 1] = (qv && oc >= -2 && oc <= 2) ? a.k[0][5 * q + oc + 2] : TS(0);
-      if (dq < 1) {
-        const int of = Pf - pq;
-        wzf[dq + 1] = (hf && qv && of >= -2 && of <= 2) ? a.k[0][5 * q + of + 2] : TS(0);
-      }
-    }
+    for (int i = 0; i < 3; ++i) wzc[i] = pwt[8 * te + i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) wzf[i] = pwt[8 * te + 3 + i];
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int j = warp * RPW + k;
@@ -937,8 +987,9 @@ __global__ void __launch_bounds__(NW * 32, level_ctas_per_sm(NW)) k_level(const 
 
 // ---------------------------------------------------------------------------
 // Recomposition interpolation (Sec. II.A, recomposition): level-l values
-// v = c + (P_z x P_y x P_x) v_coarse.  A CTA owns 32 x (NW*RPW) coarse
-// (x, y) nodes and a chunk of coarse z planes; lane l / warp row k own the
+// v = c + (P_z x P_y x P_x) v_coarse.  A CTA owns LX x (NW*32/LX*RPW) coarse
+// (x, y) nodes (LX = 32, or 16 in half-warp row groups) and a chunk of
+// coarse z planes; lane l / row k of a row group own the
 // fine block {p(q), p(q)+1} x {p(q), p(q)+1} of their coarse node (the second
 // node only when a fine node lies between q and q+1).  The coarse plane tile
 // (one extra row and column for the right / lower neighbours) is staged in
@@ -963,27 +1014,34 @@ struct InterpArgs {
   double qs;  // QZ: bin width of the level's class
 };
 
-template <int NW, int RPW, typename TD, typename TW>
+// Row groups of LX lanes (a warp, or half of one for fields with short coarse
+// rows): a CTA of NW warps owns LX x (NW * 32 / LX * RPW) coarse nodes.
+template <int NW, int RPW, typename TD, typename TW, int LX = 32>
 constexpr size_t interp_smem_bytes() {
-  return sizeof(TD) * 2 * 2 * (2 * NW * RPW) * 64 + sizeof(TW) * 2 * (NW * RPW + 1) * 33;
+  constexpr int BY = NW * 32 / LX * RPW, TC = LX == 32 ? 33 : 24;
+  return sizeof(TD) * 2 * 2 * (2 * BY) * (2 * LX) + sizeof(TW) * 2 * (BY + 1) * TC;
 }
 
 // PK: `c` is the class-packed class of this level (y_sz = n1*n2, y_sy = n2).
 // QZ (with PK): `c` holds int32 codes (TD = int), coefficient = code * qs.
-template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK = false, bool QZ = false>
+template <int NW, int RPW, typename TD, typename TO, typename TS, typename TW, bool PK = false, bool QZ = false,
+          int LX = 32>
 __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx, int by, int bz,
                                             unsigned char* smem_raw) {
-  constexpr int BY = NW * RPW, TR = BY + 1, TC = 33, RR = 2 * BY, RC = 64;
+  static_assert(LX == 32 || LX == 16, "row groups of a warp or half a warp");
+  // coarse tile pitch: LX + 1 columns, padded for half-warp groups so that
+  // the two halves of a warp (RPW rows apart) read different banks
+  constexpr int BY = NW * 32 / LX * RPW, TR = BY + 1, TC = LX == 32 ? 33 : 24, RR = 2 * BY, RC = 2 * LX;
   using TD2 = typename Pair<TD>::type;
   TD* stage = reinterpret_cast<TD*>(smem_raw);                                  // [2][2][RR][RC]
   TW* tile = reinterpret_cast<TW*>(smem_raw + sizeof(TD) * 2 * 2 * RR * RC);  // [2][TR][TC]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x % LX, warp = threadIdx.x / LX;  // lane in the row group, row group
   const int nz = a.n[0], ny = a.n[1], nx = a.n[2];
   const int mz = a.m[0], my = a.m[1], mx = a.m[2];
-  const int qx0 = bx * 32, qy0 = by * BY;
+  const int qx0 = bx * LX, qy0 = by * BY;
   const int qz0 = bz * a.qz_chunk, qz1 = min(qz0 + a.qz_chunk, mz);
   const int t_end = min(qz1, mz - 1);
-  const int tcols = min(TC, mx - qx0), trows = min(TR, my - qy0);
+  const int tcols = min(LX + 1, mx - qx0), trows = min(TR, my - qy0);
   const TD* __restrict__ cin = static_cast<const TD*>(a.c);
   const bool cz = cin == nullptr;  // coefficients of a dropped class: zero
   const TS qs = QZ ? TS(a.qs) : TS(1);

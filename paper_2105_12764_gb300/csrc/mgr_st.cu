@@ -217,7 +217,7 @@ cudaError_t launch_level_st(const mgr_plan* p, LevelArgs<TS, TW>& a, Slabs sl, i
   using G = LevelTile<C::NW, C::RPW>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
-  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], level_ctas_per_sm(C::NW));
+  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], level_ctas_per_sm(C::NW), kLevelMaxChunk);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   sl.zchunks = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
   auto kern = k_level_st<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW>;
