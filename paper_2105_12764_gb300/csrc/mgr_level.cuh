@@ -714,8 +714,11 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         c[2] = (vx0 && vy1[k]) ? c[2] : TS(0);
         c[3] = (vx1 && vy1[k]) ? c[3] : TS(0);
       }
-      *reinterpret_cast<TS2*>(cc + r0 * CP + cx0) = TS2{c[0], c[1]};
-      *reinterpret_cast<TS2*>(cc + (r0 + 1) * CP + cx0) = TS2{c[2], c[3]};
+      if constexpr (!BF) {
+        *reinterpret_cast<TS2*>(cc + r0 * CP + cx0) = TS2{c[0], c[1]};
+        *reinterpret_cast<TS2*>(cc + (r0 + 1) * CP + cx0) = TS2{c[2], c[3]};
+      }
+      TS dd[4] = {TS(0), TS(0), TS(0), TS(0)};  // fine-plane coefficients (zeros without a fine plane)
       if (PK && wy && own_c) {
         // packed class: the coarse row gy0 keeps only its fine column gx1
         const int r0 = yr0[k] - cidx(gy0[k]) * mx, r1 = yr1[k] - cidx(gy0[k] + 1) * mx;
@@ -770,18 +773,23 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
           d[2] = (vx0 && vy1[k]) ? d[2] : TS(0);
           d[3] = (vx1 && vy1[k]) ? d[3] : TS(0);
         }
-        *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
-        *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
+        if constexpr (!BF) {
+          *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{d[0], d[1]};
+          *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{d[2], d[3]};
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dd[e] = d[e];
         if (!RS && wy && own_f) {
           LVL_YP(yzf + yr0[k] + yc0, yzf + yr0[k] + yc1, yval(d[0], owy0[k] && owx0), yval(d[1], owy0[k] && owx1), owy0[k] && owx0,
                          owy0[k] && owx1, ycontig);
           LVL_YP(yzf + yr1[k] + yc0, yzf + yr1[k] + yc1, yval(d[2], owy1[k] && owx0), yval(d[3], owy1[k] && owx1), owy1[k] && owx0,
                          owy1[k] && owx1, ycontig);
         }
-      } else if constexpr (BF) {
-        // no fine plane: its stencils run on zeros
-        *reinterpret_cast<TS2*>(cf + r0 * CP + cx0) = TS2{TS(0), TS(0)};
-        *reinterpret_cast<TS2*>(cf + (r0 + 1) * CP + cx0) = TS2{TS(0), TS(0)};
+      }
+      if constexpr (BF) {
+        // FP32: both planes interleaved, {coarse plane, fine plane} per node
+        *reinterpret_cast<float4*>(cbuf + 2 * (r0 * CP + cx0)) = make_float4(c[0], dd[0], c[1], dd[1]);
+        *reinterpret_cast<float4*>(cbuf + 2 * ((r0 + 1) * CP + cx0)) = make_float4(c[2], dd[2], c[3], dd[3]);
       }
     }
     __syncthreads();
@@ -798,13 +806,16 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
             const int r = 2 * (warp * RPW + k) + h;
             const bool orow = h == 0 ? owy0[k] : owy1[k];
             const int yr = h == 0 ? yr0[k] : yr1[k];
+            // {coarse plane, fine plane} pairs of the interleaved tile
+            const float2 v0 = *reinterpret_cast<const float2*>(cbuf + 2 * (r * CP + rsl0));
+            const float2 v1 = *reinterpret_cast<const float2*>(cbuf + 2 * (r * CP + rsl1));
             if (orow && own_c) {
-              if (rs0) LVL_Y(yzc + yr + ro0, TD(cc[r * CP + rsl0]));
-              if (rs1) LVL_Y(yzc + yr + ro1, TD(cc[r * CP + rsl1]));
+              if (rs0) LVL_Y(yzc + yr + ro0, TD(v0.x));
+              if (rs1) LVL_Y(yzc + yr + ro1, TD(v1.x));
             }
             if (orow && own_f) {
-              if (rs0) LVL_Y(yzf + yr + ro0, TD(cf[r * CP + rsl0]));
-              if (rs1) LVL_Y(yzf + yr + ro1, TD(cf[r * CP + rsl1]));
+              if (rs0) LVL_Y(yzf + yr + ro0, TD(v0.y));
+              if (rs1) LVL_Y(yzf + yr + ro1, TD(v1.y));
             }
           }
         }
@@ -812,44 +823,46 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     }
 
     // ---- x stencil on every row of this warp (both planes)
-    if (BF && kxo && kx_generic) {
-      // every row's five taps from (aligned pair, pair, single) loads, both planes
+    if constexpr (BF) {
+      // FP32, both planes at once: {coarse, fine} pairs in the interleaved
+      // tiles, paired FMAs (the results equal two scalar FMA chains)
+      if (kxo && kx_generic) {
+        // every row's five taps from two 16-byte loads and one 8-byte load
 #pragma unroll
-      for (int k = 0; k < RPW; ++k) {
+        for (int k = 0; k < RPW; ++k) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = 2 * (warp * RPW + k) + h;
-          const TS* row = cc + r * CP + dx - 2;
-          const TS* rf = cf + r * CP + dx - 2;
-          const TS2 a01 = *reinterpret_cast<const TS2*>(row);
-          const TS2 a23 = *reinterpret_cast<const TS2*>(row + 2);
-          const TS2 b01 = *reinterpret_cast<const TS2*>(rf);
-          const TS2 b23 = *reinterpret_cast<const TS2*>(rf + 2);
-          gxb[r * GP + lane] = kx(0) * a01.x + kx(1) * a01.y + kx(2) * a23.x + kx(3) * a23.y + kx(4) * row[4];
-          gxb[RR * GP + r * GP + lane] = kx(0) * b01.x + kx(1) * b01.y + kx(2) * b23.x + kx(3) * b23.y + kx(4) * rf[4];
-        }
-      }
-    } else if (BF && kxo) {
-      // boundary columns: clamped slots, weight 0 outside the grid
-#pragma unroll
-      for (int k = 0; k < RPW; ++k) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = 2 * (warp * RPW + k) + h;
-          const TS* row = cc + r * CP;
-          const TS* rf = cf + r * CP;
-          TS g = TS(0), gf = TS(0);
-#pragma unroll
-          for (int o = 0; o < 5; ++o) {
-            const int j = min(max(dx - 2 + o, 0), RC - 1);  // weight 0 where clamped
-            g += kx(o) * row[j];
-            gf += kx(o) * rf[j];
+          for (int h = 0; h < 2; ++h) {
+            const int r = 2 * (warp * RPW + k) + h;
+            const float* row = cbuf + 2 * (r * CP + dx - 2);
+            const float4 t01 = *reinterpret_cast<const float4*>(row);
+            const float4 t23 = *reinterpret_cast<const float4*>(row + 4);
+            const float2 t4 = *reinterpret_cast<const float2*>(row + 8);
+            float2 g = __fmul2_rn(make_float2(kx(0), kx(0)), make_float2(t01.x, t01.y));
+            g = __ffma2_rn(make_float2(kx(1), kx(1)), make_float2(t01.z, t01.w), g);
+            g = __ffma2_rn(make_float2(kx(2), kx(2)), make_float2(t23.x, t23.y), g);
+            g = __ffma2_rn(make_float2(kx(3), kx(3)), make_float2(t23.z, t23.w), g);
+            g = __ffma2_rn(make_float2(kx(4), kx(4)), t4, g);
+            *reinterpret_cast<float2*>(gxb + 2 * (r * GP + lane)) = g;
           }
-          gxb[r * GP + lane] = g;
-          gxb[RR * GP + r * GP + lane] = gf;
+        }
+      } else if (kxo) {
+        // boundary columns: clamped slots, weight 0 outside the grid
+#pragma unroll
+        for (int k = 0; k < RPW; ++k) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = 2 * (warp * RPW + k) + h;
+            float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) {
+              const int j = min(max(dx - 2 + o, 0), RC - 1);  // weight 0 where clamped
+              g = __ffma2_rn(make_float2(kx(o), kx(o)), *reinterpret_cast<const float2*>(cbuf + 2 * (r * CP + j)), g);
+            }
+            *reinterpret_cast<float2*>(gxb + 2 * (r * GP + lane)) = g;
+          }
         }
       }
-    } else if (!BF && kxo) {
+    } else if (kxo) {
 #pragma unroll
       for (int k = 0; k < RPW; ++k) {
 #pragma unroll
@@ -900,25 +913,26 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     for (int k = 0; k < RPW; ++k) {
       const int j = warp * RPW + k;
       if constexpr (BF) {
-        // both planes, five taps each; rows clamped into the tile (weight 0 where clamped);
-        // computed on every lane, stored only where the output exists
-        const TS* gcol = gxb + lane;
-        TS gc = TS(0), gf = TS(0);
+        // both planes at once ({coarse, fine} pairs, paired FMAs), five taps;
+        // rows clamped into the tile (weight 0 where clamped); computed on
+        // every lane, stored only where the output exists
+        const float* gcol = gxb + 2 * lane;
+        float2 g;
         if (kym[k] == 31u) {
-          const TS* g0 = gcol + (dyo[k] - 2) * GP;
-          gc = ky(k, 0) * g0[0] + ky(k, 1) * g0[GP] + ky(k, 2) * g0[2 * GP] + ky(k, 3) * g0[3 * GP] +
-               ky(k, 4) * g0[4 * GP];
-          const TS* f0 = g0 + RR * GP;
-          gf = ky(k, 0) * f0[0] + ky(k, 1) * f0[GP] + ky(k, 2) * f0[2 * GP] + ky(k, 3) * f0[3 * GP] +
-               ky(k, 4) * f0[4 * GP];
+          const float* g0 = gcol + 2 * (dyo[k] - 2) * GP;
+          g = __fmul2_rn(make_float2(ky(k, 0), ky(k, 0)), *reinterpret_cast<const float2*>(g0));
+#pragma unroll
+          for (int o = 1; o < 5; ++o)
+            g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(g0 + 2 * o * GP), g);
         } else {
+          g = make_float2(0.f, 0.f);
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
             const int rr = min(max(dyo[k] + o - 2, 0), RR - 1);
-            gc += ky(k, o) * gcol[rr * GP];
-            gf += ky(k, o) * gcol[RR * GP + rr * GP];
+            g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(gcol + 2 * rr * GP), g);
           }
         }
+        const TS gc = g.x, gf = g.y;
         acc0[k] += wzc[0] * gc;
         acc1[k] += wzc[1] * gc;
         acc2[k] += wzc[2] * gc;
