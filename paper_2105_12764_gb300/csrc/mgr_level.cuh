@@ -603,7 +603,11 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
     } else {
       cp_wait<0>();
     }
-    __syncthreads();
+    // Every thread copies, and later reads, only its own slots of the stage
+    // buffer; the one exception is FP32's read of the next warp's first row
+    // (nxt0 / nxt1 below), which needs the CTA barrier.
+    if constexpr (BF) __syncthreads();
+    else __syncwarp();
     const TI* sc = stage_of(t);
     const TI* sf = sc + RR * RC;
     const int te = t - t_start;
@@ -792,7 +796,14 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
         *reinterpret_cast<float4*>(cbuf + 2 * ((r0 + 1) * CP + cx0)) = make_float4(c[2], dd[2], c[3], dd[3]);
       }
     }
-    __syncthreads();
+    // The x stencil and the row stores read only this warp's rows of the
+    // coefficient tile: a warp barrier orders them.  With one stage buffer,
+    // FP32 reloads the buffer whose rows the warp above still reads (nxt0 /
+    // nxt1): a CTA barrier then.  (The x-stencil results that the y stencil
+    // reads across warps are written after the previous plane pair's last CTA
+    // barrier and read after this one's.)
+    if constexpr (BF && STAGES == 1) __syncthreads();
+    else __syncwarp();
 
     if (STAGES == 1 && t < t_end) issue(t + 1);  // every thread is done with the stage buffer
 
