@@ -448,7 +448,7 @@ struct Builder {
     ph.n_items = int(items.size());
     ph.fn = reinterpret_cast<const void*>(kb_interp<NW, RPW, TD, TO, TS, TW, LX>);
     ph.block = NW * 32;
-    ph.smem = interp_smem_bytes<NW, RPW, TD, TW, LX>();
+    ph.smem = interp_smem_bytes<NW, RPW, TD, TS, TW, LX>();
     ph.grid = std::min(ph.n_items, num_sms * level_ctas_per_sm(NW));
     pending.push_back(ph);
   }

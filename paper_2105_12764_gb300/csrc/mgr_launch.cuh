@@ -181,7 +181,7 @@ InterpArgs<TS, TW> interp_args(const mgr_plan* p, int l, const void* c, const TW
 // z chunking of an interpolation launch (sets a.qz_chunk; returns the chunk count)
 template <typename TS, typename TW>
 int interp_chunks(const mgr_plan* p, InterpArgs<TS, TW>& a, int gx, int gy) {
-  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2);
+  const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], 2, kLevelMaxChunk);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   return (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
 }
@@ -196,7 +196,7 @@ void launch_interp_chunks(const mgr_plan* p, int l, const void* c, const TW* w, 
   if (c1 < 0) c1 = gz;
   if (c1 <= c0 || c1 > gz) return;
   a.bz0 = c0;
-  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
+  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TS, TW>();
   auto kern = k_interp<kInterpNW, kInterpRPW, TD, TO, TS, TW, PK, QZ>;
   raise_smem_limit(kern, sm);
   kern<<<dim3(gx, gy, c1 - c0), kInterpNW * 32, sm, st>>>(a);

@@ -1042,9 +1042,14 @@ struct InterpArgs {
 // Row groups of LX lanes (a warp, or half of one for fields with short coarse
 // rows): a CTA of NW warps owns LX x (NW * 32 / LX * RPW) coarse nodes.
 template <int NW, int RPW, typename TD, typename TW, int LX = 32>
-constexpr size_t interp_smem_bytes() {
+constexpr size_t interp_table_offset() {
   constexpr int BY = NW * 32 / LX * RPW, TC = LX == 32 ? 33 : 24;
-  return sizeof(TD) * 2 * 2 * (2 * BY) * (2 * LX) + sizeof(TW) * 2 * (BY + 1) * TC;
+  return (sizeof(TD) * 2 * 2 * (2 * BY) * (2 * LX) + sizeof(TW) * 2 * (BY + 1) * TC + 15) / 16 * 16;
+}
+// plane table: per plane pair six offsets (int64), two weights, a flag
+template <int NW, int RPW, typename TD, typename TS, typename TW, int LX = 32>
+constexpr size_t interp_smem_bytes() {
+  return interp_table_offset<NW, RPW, TD, TW, LX>() + kLevelPlanes * (6 * sizeof(int64_t) + 2 * sizeof(TS) + sizeof(int));
 }
 
 // PK: `c` is the class-packed class of this level (y_sz = n1*n2, y_sy = n2).
@@ -1131,12 +1136,50 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     or1[k] = (a.out_full ? fmap(g1, a.s[1], a.N[1]) : int64_t(g1)) * a.o_sy;
   }
 
-  auto has_fine = [&](int t) { return t > qz0 && pidx(t, nz) - pidx(t - 1, nz) == 2; };
-  // zc: gz is a coarse plane
-  auto load_c = [&](TD* sb, int gz, bool zc) {
+  // ---- plane table, computed once by the CTA (instead of by every warp on
+  // every plane pair): entry t - qz0 holds the offsets of plane pair t's
+  // coefficient planes (coarse p(t), and the fine plane before it when there
+  // is one), of its output planes, of the coarse values' plane t, and the
+  // fine plane's z interpolation weights
+  int64_t* itab = reinterpret_cast<int64_t*>(smem_raw + interp_table_offset<NW, RPW, TD, TW, LX>());
+  TS* iwt = reinterpret_cast<TS*>(itab + 6 * kLevelPlanes);
+  int* ifl = reinterpret_cast<int*>(iwt + 2 * kLevelPlanes);
+  auto cplane = [&](int g) -> int64_t {
+    return PK ? int64_t(g) * a.y_sz - int64_t(cidx(g)) * a.c_sz : fmap(g, a.s[0], a.N[0]) * a.y_sz;
+  };
+  auto oplane = [&](int g) -> int64_t { return (a.out_full ? fmap(g, a.s[0], a.N[0]) : int64_t(g)) * a.o_sz; };
+  (void)MGR_IN(t_end - qz0, kLevelPlanes, kDbgInterpStage);
+  for (int e = threadIdx.x; e <= t_end - qz0 && e < kLevelPlanes; e += NW * 32) {
+    const int t = qz0 + e, Pc = pidx(t, nz), Pf = Pc - 1;
+    const bool hf = t > qz0 && Pc - pidx(t - 1, nz) == 2;
+    itab[6 * e + 0] = cplane(Pc);
+    itab[6 * e + 1] = hf ? cplane(Pf) : 0;
+    itab[6 * e + 2] = oplane(Pc);
+    itab[6 * e + 3] = oplane(max(Pf, 0));
+    itab[6 * e + 4] = int64_t(t) * a.c_sz;
+    iwt[2 * e + 0] = hf ? a.wa[0][Pf] : TS(0);
+    iwt[2 * e + 1] = hf ? a.wb[0][Pf] : TS(0);
+    ifl[e] = hf ? 1 : 0;
+  }
+  // this thread's copies of the coarse tile: offsets in the coarse plane
+  // (-1: none) and slots
+  constexpr int KT = (TR * TC + NW * 32 - 1) / (NW * 32);
+  int tgo[KT], tso[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) {
+    const int e = threadIdx.x + i * NW * 32;
+    const int r = e / TC, cix = e - r * TC;
+    tgo[i] = (e < trows * TC && cix < tcols) ? int(int64_t(r) * a.c_sy + cix) : -1;
+    tso[i] = r * TC + cix;
+  }
+  const int64_t wtile0 = int64_t(qy0) * a.c_sy + qx0;
+  __syncthreads();  // plane table staged
+
+  // coefficient plane at offset poff of `cin`; zc: a coarse plane
+  auto load_c = [&](TD* sb, int64_t poff, bool zc) {
     if (cz) return;
     if constexpr (PK) {
-      const TD* base = cin + int64_t(gz) * a.y_sz - int64_t(cidx(gz)) * a.c_sz;
+      const TD* base = cin + poff;
 #pragma unroll
       for (int k = 0; k < RPW; ++k) {
         const int r0 = 2 * (warp * RPW + k);
@@ -1154,7 +1197,7 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
       }
       return;
     }
-    const TD* base = cin + fmap(gz, a.s[0], a.N[0]) * a.y_sz;
+    const TD* base = cin + poff;
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int r0 = 2 * (warp * RPW + k);
@@ -1165,18 +1208,16 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     }
   };
   auto issue = [&](int t) {
-    const int st = (t - qz0) & 1;
+    const int e = t - qz0, st = e & 1;
     TW* tb = tile + st * TR * TC;
-    const TW* src = a.w + int64_t(t) * a.c_sz + int64_t(qy0) * a.c_sy + qx0;
-    for (int e = threadIdx.x; e < trows * TC; e += NW * 32) {
-      const int r = e / TC, cix = e - r * TC;
-      if (cix < tcols)
-        MGR_GUARD(MGR_PIN(src + int64_t(r) * a.c_sy + cix, a.w, n_w, kDbgInterpW),
-                  cp_async(tb + r * TC + cix, src + int64_t(r) * a.c_sy + cix, int(sizeof(TW))));
-    }
+    const TW* src = a.w + itab[6 * e + 4] + wtile0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i)
+      if (tgo[i] >= 0)
+        MGR_GUARD(MGR_PIN(src + tgo[i], a.w, n_w, kDbgInterpW), cp_async(tb + tso[i], src + tgo[i], int(sizeof(TW))));
     TD* sb = stage + st * 2 * RR * RC;
-    if (t < qz1) load_c(sb, pidx(t, nz), true);
-    if (has_fine(t)) load_c(sb + RR * RC, pidx(t, nz) - 1, false);
+    if (t < qz1) load_c(sb, itab[6 * e + 0], true);
+    if (ifl[e]) load_c(sb + RR * RC, itab[6 * e + 1], false);
     cp_commit();
   };
 
@@ -1209,13 +1250,12 @@ __device__ __forceinline__ void interp_body(const InterpArgs<TS, TW>& a, int bx,
     const TW* tb = tile + st * TR * TC;
     const TD* sc = stage + st * 2 * RR * RC;
     const TD* sf = sc + RR * RC;
-    const int Pc = pidx(t, nz);
+    const int te = t - qz0;
     const bool own_c = t < qz1;
-    const bool hf = has_fine(t);
-    const int Pf = Pc - 1;
-    TO* ozc = out + (a.out_full ? fmap(Pc, a.s[0], a.N[0]) : int64_t(Pc)) * a.o_sz;
-    TO* ozf = out + (a.out_full ? fmap(max(Pf, 0), a.s[0], a.N[0]) : int64_t(max(Pf, 0))) * a.o_sz;
-    const TS za = hf ? a.wa[0][Pf] : TS(0), zb = hf ? a.wb[0][Pf] : TS(0);
+    const bool hf = ifl[te] != 0;
+    TO* ozc = out + itab[6 * te + 2];
+    TO* ozf = out + itab[6 * te + 3];
+    const TS za = iwt[2 * te + 0], zb = iwt[2 * te + 1];
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
       const int r = warp * RPW + k;

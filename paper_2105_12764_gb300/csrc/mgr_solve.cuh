@@ -234,12 +234,14 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
   const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
   // rows r0 .. r0+nr-1 of mline elements at pitch row_pitch
   if (!MGR_IN((r0 + nr - 1) * row_pitch + mline - 1, rows * row_pitch, kDbgSolveF)) return;
-  const int total = nr * mline;
   // the rows go to shared memory as element-wise asynchronous copies, all in
-  // flight at once (the staging, not the recurrences, bounds this kernel)
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int r = e / mline, c = e - r * mline;
-    cp_async(s + r * pitch + c, f + (r0 + r) * row_pitch + c, int(sizeof(TW)));
+  // flight at once (the staging, not the recurrences, bounds this kernel);
+  // a warp takes whole rows, its lanes consecutive elements
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = wid; r < nr; r += nw) {
+    const TW* src = f + (r0 + r) * row_pitch;
+    TW* dst = s + r * pitch;
+    for (int c = lane; c < mline; c += 32) cp_async(dst + c, src + c, int(sizeof(TW)));
   }
   cp_commit();
   for (int q = threadIdx.x; q < mline; q += blockDim.x) {
@@ -281,26 +283,28 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
     }
   }
   __syncthreads();
-  // write back (or apply the correction to w), W elements per thread per
-  // round with their loads of w issued together
+  // write back (or apply the correction to w), a warp per row, W elements
+  // per lane per round with their loads of w issued together
   constexpr int W = 8;
-  for (int e0 = threadIdx.x; e0 < total; e0 += W * blockDim.x) {
-    int64_t g[W];
-    TW sv[W], wv[W];
+  for (int r = wid; r < nr; r += nw) {
+    const TW* srow = s + r * pitch;
+    const int64_t g0 = (r0 + r) * row_pitch;
+    for (int c0 = lane; c0 < mline; c0 += 32 * W) {
+      TW sv[W], wv[W];
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-      const int e = e0 + u * blockDim.x;
-      const int r = (e < total ? e : 0) / mline, c = (e < total ? e : 0) - r * mline;
-      g[u] = (r0 + r) * row_pitch + c;
-      sv[u] = s[r * pitch + c];
-      wv[u] = (op != SOLVE_INPLACE && e < total) ? w[g[u]] : TW(0);
-    }
+      for (int u = 0; u < W; ++u) {
+        const int c = c0 + 32 * u;
+        sv[u] = c < mline ? srow[c] : TW(0);
+        wv[u] = (op != SOLVE_INPLACE && c < mline) ? w[g0 + c] : TW(0);
+      }
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-      if (e0 + u * blockDim.x >= total) break;
-      if (op == SOLVE_INPLACE) f[g[u]] = sv[u];
-      else if (op == SOLVE_ADD) w[g[u]] = wv[u] + sv[u];
-      else w[g[u]] = wv[u] - sv[u];
+      for (int u = 0; u < W; ++u) {
+        const int c = c0 + 32 * u;
+        if (c >= mline) break;
+        if (op == SOLVE_INPLACE) f[g0 + c] = sv[u];
+        else if (op == SOLVE_ADD) w[g0 + c] = wv[u] + sv[u];
+        else w[g0 + c] = wv[u] - sv[u];
+      }
     }
   }
 }

@@ -232,10 +232,10 @@ cudaError_t launch_interp_st(const mgr_plan* p, int l, const TD* c, const TW* w,
   if (slabs <= 0) return cudaSuccess;
   int gx, gy;
   InterpArgs<TS, TW> a = interp_args<TS, TW>(p, l, c, w, out, out_full, 1.0, &gx, &gy);
-  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], 2);
+  const int chunks = choose_chunks(p, int64_t(gx) * gy * slabs, a.m[0], 2, kLevelMaxChunk);
   a.qz_chunk = (a.m[0] + chunks - 1) / chunks;
   sl.zchunks = (a.m[0] + a.qz_chunk - 1) / a.qz_chunk;
-  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TW>();
+  constexpr size_t sm = interp_smem_bytes<kInterpNW, kInterpRPW, TD, TS, TW>();
   auto kern = k_interp_st<kInterpNW, kInterpRPW, TD, TO, TS, TW>;
   raise_smem_limit(kern, sm);
   kern<<<dim3(gx, gy, sl.zchunks * slabs), kInterpNW * 32, sm, st>>>(a, sl);
