@@ -209,14 +209,21 @@ void launch_interp(const mgr_plan* p, int l, const void* c, const TW* w, void* o
 }
 
 // Thomas solves along the contiguous axis: `lines` lines of length mx,
-// consecutive in memory.
+// consecutive in memory.  Build-time knobs: MGR_X_SOLVE_ROWS (1: FP64 with
+// many lines through k_solve_rows), MGR_X_SOLVE_KB (shared memory per CTA of
+// k_solve_contig).
+#ifndef MGR_X_SOLVE_ROWS
+#define MGR_X_SOLVE_ROWS 1
+#endif
+#ifndef MGR_X_SOLVE_KB
+#define MGR_X_SOLVE_KB 32
+#endif
 template <typename TW>
 cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t lines, const TW* ta, const TW* tb, int op,
                            cudaStream_t st) {
   (void)p;
-  if (sizeof(TW) == 8 && lines >= 32768) {
-    // FP64 with many lines: the recurrences' FP64 latency needs more lines in
-    // flight per SM than whole lines staged in shared memory allow
+  if (MGR_X_SOLVE_ROWS && sizeof(TW) == 8 && lines >= 32768) {
+    // lines through 32 x 32 tiles, the intermediate through memory
     const int64_t nwarps = (lines + 31) / 32;
     k_solve_rows<TW><<<int((nwarps + kRowsWarps - 1) / kRowsWarps), kRowsWarps * 32, 0, st>>>(f, w, mx, lines, mx, ta,
                                                                                              tb, op);
@@ -230,9 +237,9 @@ cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t line
     return cudaGetLastError();
   }
   const int pitch = mx | 1;
-  // rows per CTA (one solving thread per row, 128 threads load and store):
-  // up to 32 rows within 32 KB of shared memory, so several CTAs share an SM
-  int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
+  // rows per CTA (one solving thread per row, 128 threads load and store): up
+  // to 32, a whole warp of recurrences, within MGR_X_SOLVE_KB of shared memory
+  int R = int(std::min<size_t>(32, (size_t(MGR_X_SOLVE_KB) * 1024) / (sizeof(TW) * pitch)));
   R = std::max(1, R);
   const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
   const int blocks = int((lines + R - 1) / R);
