@@ -926,31 +926,34 @@ __device__ __forceinline__ void level_body(const LevelArgs<TS, TW>& a, int bx, i
       if constexpr (BF) {
         // both planes at once ({coarse, fine} pairs, paired FMAs), five taps;
         // rows clamped into the tile (weight 0 where clamped); computed on
-        // every lane, stored only where the output exists
-        const float* gcol = gxb + 2 * lane;
-        float2 g;
-        if (kym[k] == 31u) {
-          const float* g0 = gcol + 2 * (dyo[k] - 2) * GP;
-          g = __fmul2_rn(make_float2(ky(k, 0), ky(k, 0)), *reinterpret_cast<const float2*>(g0));
+        // every lane of a row slot with outputs (j < nby: uniform across the
+        // row group), stored only where the output exists
+        if (j < nby) {
+          const float* gcol = gxb + 2 * lane;
+          float2 g;
+          if (kym[k] == 31u) {
+            const float* g0 = gcol + 2 * (dyo[k] - 2) * GP;
+            g = __fmul2_rn(make_float2(ky(k, 0), ky(k, 0)), *reinterpret_cast<const float2*>(g0));
 #pragma unroll
-          for (int o = 1; o < 5; ++o)
-            g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(g0 + 2 * o * GP), g);
-        } else {
-          g = make_float2(0.f, 0.f);
+            for (int o = 1; o < 5; ++o)
+              g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(g0 + 2 * o * GP), g);
+          } else {
+            g = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int o = 0; o < 5; ++o) {
-            const int rr = min(max(dyo[k] + o - 2, 0), RR - 1);
-            g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(gcol + 2 * rr * GP), g);
+            for (int o = 0; o < 5; ++o) {
+              const int rr = min(max(dyo[k] + o - 2, 0), RR - 1);
+              g = __ffma2_rn(make_float2(ky(k, o), ky(k, o)), *reinterpret_cast<const float2*>(gcol + 2 * rr * GP), g);
+            }
           }
+          const TS gc = g.x, gf = g.y;
+          acc0[k] += wzc[0] * gc;
+          acc1[k] += wzc[1] * gc;
+          acc2[k] += wzc[2] * gc;
+          acc0[k] += wzf[0] * gf;
+          acc1[k] += wzf[1] * gf;
+          if (kxo && t - 1 >= qz0 && t - 1 < qz1)
+            LVL_F(int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
         }
-        const TS gc = g.x, gf = g.y;
-        acc0[k] += wzc[0] * gc;
-        acc1[k] += wzc[1] * gc;
-        acc2[k] += wzc[2] * gc;
-        acc0[k] += wzf[0] * gf;
-        acc1[k] += wzf[1] * gf;
-        if (j < nby && kxo && t - 1 >= qz0 && t - 1 < qz1)
-          LVL_F(int64_t(t - 1) * a.c_sz + int64_t(qy0 + j) * a.c_sy + qxo, fout(acc0[k]));
       } else if (j < nby && kxo) {
         TS gc = TS(0), gf = TS(0);
         const TS* gcol = gxb + (dyo[k] - 2) * GP + lane;

@@ -52,6 +52,30 @@ constexpr size_t small_smem_bytes(int n0, int n1, int n2, int m0, int m1, int m2
          sizeof(TS) * (size_t(n0) * n1 * m2 + size_t(n0) * m1 * m2) + 64;
 }
 
+// Index arithmetic of the element loops: n / d and n % d for 0 <= n < 2^22 and a
+// divisor d >= 1 fixed for the loop, from the single-precision reciprocal of d
+// taken once.  float(n) is exact, and fl(n * fl(1/d)) is within a relative
+// 2^-23 of n/d, so below 2^22 its truncation q0 is floor(n/d) or one off;
+// the remainder n - q0*d says which way and one step corrects it.  (A runtime
+// integer division is a long instruction sequence; these loops do a few per
+// element.)
+struct SmallDiv {
+  int d;
+  float rd;
+  __device__ explicit SmallDiv(int divisor) : d(divisor), rd(1.0f / float(divisor)) {}
+  __device__ __forceinline__ int quo(int n) const {
+    int q = int(float(n) * rd);
+    const int r = n - q * d;
+    return q + (r >= d ? 1 : 0) - (r < 0 ? 1 : 0);
+  }
+  // (q, r) with n = q*d + r, 0 <= r < d
+  __device__ __forceinline__ int quo_rem(int n, int& r) const {
+    const int q = quo(n);
+    r = n - q * d;
+    return q;
+  }
+};
+
 __device__ __forceinline__ int64_t small_full(const int64_t* s, const int64_t* N, int i0, int i1, int i2, int64_t sz,
                                                int64_t sy) {
   return fmap(i0, s[0], N[0]) * sz + fmap(i1, s[1], N[1]) * sy + fmap(i2, s[2], N[2]);
@@ -113,8 +137,10 @@ template <typename TS, typename TW>
 __device__ __forceinline__ void small_load_vector(const TW* c, TS* t1, TS* t2, TW* f, const int* n, const int* m,
                                                   const TS* const* K) {
   const int n0 = n[0], n1 = n[1], n2 = n[2], m0 = m[0], m1 = m[1], m2 = m[2];
+  const SmallDiv dm2(m2), dm1(m1), dm12(m1 * m2);
   for (int e = threadIdx.x; e < n0 * n1 * m2; e += blockDim.x) {
-    const int q = e % m2, r = e / m2;
+    int q;
+    const int r = dm2.quo_rem(e, q);
     const int p = pidx(q, n2);
     TS acc = TS(0);
     for (int o = 0; o < 5; ++o) {
@@ -125,7 +151,8 @@ __device__ __forceinline__ void small_load_vector(const TW* c, TS* t1, TS* t2, T
   }
   __syncthreads();
   for (int e = threadIdx.x; e < n0 * m1 * m2; e += blockDim.x) {
-    const int x = e % m2, q = (e / m2) % m1, i0 = e / (m1 * m2);
+    int x, q;
+    const int i0 = dm1.quo_rem(dm2.quo_rem(e, x), q);
     const int p = pidx(q, n1);
     TS acc = TS(0);
     for (int o = 0; o < 5; ++o) {
@@ -136,7 +163,8 @@ __device__ __forceinline__ void small_load_vector(const TW* c, TS* t1, TS* t2, T
   }
   __syncthreads();
   for (int e = threadIdx.x; e < m0 * m1 * m2; e += blockDim.x) {
-    const int yx = e % (m1 * m2), q = e / (m1 * m2);
+    int yx;
+    const int q = dm12.quo_rem(e, yx);
     const int p = pidx(q, n0);
     TS acc = TS(0);
     for (int o = 0; o < 5; ++o) {
@@ -158,12 +186,14 @@ __device__ __forceinline__ void small_solves(TW* f, const int* m, const int* act
     const int len = m[axis];
     const int lines = m0 * m1 * m2 / len;
     const int stride = axis == 2 ? 1 : (axis == 1 ? m2 : m1 * m2);
+    const SmallDiv dm2(m2);
     for (int li = threadIdx.x; li < lines; li += blockDim.x) {
       int base;
       if (axis == 2) {
         base = li * m2;
       } else if (axis == 1) {
-        base = (li / m2) * m1 * m2 + li % m2;
+        int x;
+        base = dm2.quo_rem(li, x) * m1 * m2 + x;
       } else {
         base = li;
       }
@@ -197,10 +227,11 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
   TD* out = static_cast<TD*>(a.out);
   // level-ls values
   {
-    const int n1 = a.n[ls][1], n2 = a.n[ls][2];
-    for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
+    const SmallDiv dn1(a.n[ls][1]), dn2(a.n[ls][2]);
+    for (int e = threadIdx.x; e < int(nv); e += blockDim.x) {
       if (a.vin_full) {
-        const int i2 = int(e % n2), i1 = int((e / n2) % n1), i0 = int(e / (int64_t(n1) * n2));
+        int i1, i2;
+        const int i0 = dn1.quo_rem(dn2.quo_rem(e, i2), i1);
         V[e] = TW(small_ld(static_cast<const TD*>(a.vin), small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
       } else {
         V[e] = static_cast<const TW*>(a.vin)[e];
@@ -212,15 +243,18 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
     const int* n = a.n[l];
     const int* m = a.m[l];
     const int ln = n[0] * n[1] * n[2], lm = m[0] * m[1] * m[2];
+    const SmallDiv dn1(n[1]), dn2(n[2]), dm1(m[1]), dm2(m[2]);
     // coarse values
     for (int e = threadIdx.x; e < lm; e += blockDim.x) {
-      const int q2 = e % m[2], q1 = (e / m[2]) % m[1], q0 = e / (m[1] * m[2]);
+      int q1, q2;
+      const int q0 = dm1.quo_rem(dm2.quo_rem(e, q2), q1);
       W[e] = V[(int64_t(pidx(q0, n[0])) * n[1] + pidx(q1, n[1])) * n[2] + pidx(q2, n[2])];
     }
     __syncthreads();
     // coefficients (in place), written to their nodal positions
     for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-      const int i2 = e % n[2], i1 = (e / n[2]) % n[1], i0 = e / (n[1] * n[2]);
+      int i1, i2;
+      const int i0 = dn1.quo_rem(dn2.quo_rem(e, i2), i1);
       if (is_coarse(i0, n[0]) && is_coarse(i1, n[1]) && is_coarse(i2, n[2])) {
         V[e] = TW(0);
         continue;
@@ -238,8 +272,10 @@ __device__ __forceinline__ void small_dec_body(const SmallArgs<TS, TW>& a, unsig
   }
   // coarsest values
   const int c0 = a.n0[0], c1 = a.n0[1], c2 = a.n0[2];
+  const SmallDiv dc1(c1), dc2(c2);
   for (int e = threadIdx.x; e < c0 * c1 * c2; e += blockDim.x) {
-    const int i2 = e % c2, i1 = (e / c2) % c1, i0 = e / (c1 * c2);
+    int i1, i2;
+    const int i0 = dc1.quo_rem(dc2.quo_rem(e, i2), i1);
     small_st(out, small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy), TD(V[e]), a.N, a.sz);
   }
 }
@@ -265,8 +301,10 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
   // coarsest values
   {
     const int c0 = a.n0[0], c1 = a.n0[1], c2 = a.n0[2];
+    const SmallDiv dc1(c1), dc2(c2);
     for (int e = threadIdx.x; e < c0 * c1 * c2; e += blockDim.x) {
-      const int i2 = e % c2, i1 = (e / c2) % c1, i0 = e / (c1 * c2);
+      int i1, i2;
+      const int i0 = dc1.quo_rem(dc2.quo_rem(e, i2), i1);
       W[e] = TW(small_ld(cin, small_full(a.s0, a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
     }
   }
@@ -275,9 +313,11 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
     const int* n = a.n[l];
     const int* m = a.m[l];
     const int ln = n[0] * n[1] * n[2], lm = m[0] * m[1] * m[2];
+    const SmallDiv dn1(n[1]), dn2(n[2]);
     // this level's coefficients (0 on the coarse nodes)
     for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-      const int i2 = e % n[2], i1 = (e / n[2]) % n[1], i0 = e / (n[1] * n[2]);
+      int i1, i2;
+      const int i0 = dn1.quo_rem(dn2.quo_rem(e, i2), i1);
       const bool coarse = is_coarse(i0, n[0]) && is_coarse(i1, n[1]) && is_coarse(i2, n[2]);
       V[e] = coarse ? TW(0) : TW(small_ld(cin, small_full(a.s[l], a.N, i0, i1, i2, a.sz, a.sy), a.N, a.sz));
     }
@@ -288,7 +328,8 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
     __syncthreads();
     // level values: coefficients plus the interpolant of the coarse values
     for (int e = threadIdx.x; e < ln; e += blockDim.x) {
-      const int i2 = e % n[2], i1 = (e / n[2]) % n[1], i0 = e / (n[1] * n[2]);
+      int i1, i2;
+      const int i0 = dn1.quo_rem(dn2.quo_rem(e, i2), i1);
       if (is_coarse(i0, n[0]) && is_coarse(i1, n[1]) && is_coarse(i2, n[2])) {
         V[e] = W[(int64_t(cidx(i0)) * m[1] + cidx(i1)) * m[2] + cidx(i2)];
       } else {
@@ -302,10 +343,11 @@ __device__ __forceinline__ void small_rec_body(const SmallArgs<TS, TW>& a, unsig
     }
   }
   // level-ls values
-  const int n1 = a.n[ls][1], n2 = a.n[ls][2];
-  for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) {
+  const SmallDiv dn1(a.n[ls][1]), dn2(a.n[ls][2]);
+  for (int e = threadIdx.x; e < int(nv); e += blockDim.x) {
     if (a.vout_full) {
-      const int i2 = int(e % n2), i1 = int((e / n2) % n1), i0 = int(e / (int64_t(n1) * n2));
+      int i1, i2;
+      const int i0 = dn1.quo_rem(dn2.quo_rem(e, i2), i1);
       small_st(static_cast<TD*>(a.vout), small_full(a.s[ls], a.N, i0, i1, i2, a.sz, a.sy), TD(V[e]), a.N, a.sz);
     } else {
       static_cast<TW*>(a.vout)[e] = V[e];
