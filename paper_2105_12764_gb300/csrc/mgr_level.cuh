@@ -27,10 +27,13 @@
 // each thread keeps in registers.
 //
 // Load vector f' = (x_k D_k^-1 K_k) c (Sec. II.A.2, III.A.2): c goes to
-// shared memory, the x stencil runs on rows (5 taps; 2 on rows that are
-// coarse in y and z, where c vanishes on coarse nodes), the y stencil on
+// shared memory, the x stencil runs on rows (5 taps; in FP64 2 on rows that
+// are coarse in y and z, where c vanishes on coarse nodes), the y stencil on
 // the x results, and the z stencil accumulates in registers over the
-// streamed planes.  Three barriers per plane pair (FP32) or four (FP64).
+// streamed planes.  FP32 keeps the two planes interleaved in its tiles
+// ({coarse, fine} per node) and runs both planes' stencils as paired FMAs.
+// The per-plane-pair constants come from a table the CTA fills once.  Two
+// CTA barriers per plane pair.
 //
 // Coefficient addressing.  Nodal (PK = false): a coefficient sits at its node's
 // full-grid position.  Class-packed (PK = true, Sec. I coefficient classes): the
