@@ -477,16 +477,15 @@ struct Builder {
       s.ta = T + g.ax[axis].o_ta;
       s.tb = T + g.ax[axis].o_tb;
       s.op = (axis == last) ? final_op : SOLVE_INPLACE;
-      const size_t stage = sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx));
-      if (axis == 2 && stage <= 96 * 1024) {
-        const int pitch = mx | 1;
+      if (axis == 2 && solve_contig_smem<TW>(mx, 1) <= 96 * 1024) {
+        const int pitch = contig_pitch<TW>(mx);
         int R = int(std::min<size_t>(32, (32 * 1024) / (sizeof(TW) * pitch)));
         R = std::max(1, R);
         s.mline = mx;
         s.count = int64_t(mz) * my;
         s.row_pitch = mx;
         s.R = R;
-        csmem = std::max(csmem, sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx)));
+        csmem = std::max(csmem, solve_contig_smem<TW>(mx, R));
         const int di = int(cdesc.size());
         cdesc.push_back(s);
         const int64_t blocks = (s.count + R - 1) / R;

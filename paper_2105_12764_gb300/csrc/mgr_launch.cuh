@@ -229,19 +229,19 @@ cudaError_t launch_x_solve(const mgr_plan* p, TW* f, TW* w, int mx, int64_t line
                                                                                              tb, op);
     return cudaGetLastError();
   }
-  if (sizeof(TW) * (size_t(mx | 1) + 2 * size_t(mx)) > 96 * 1024) {
+  if (solve_contig_smem<TW>(mx, 1) > 96 * 1024) {
     // lines too long to stage in shared memory: one thread per line from global memory
     const int threads = 128;
     const int blocks = int((lines + threads - 1) / threads);
     k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mx, 1, 1, lines, mx, ta, tb, op);
     return cudaGetLastError();
   }
-  const int pitch = mx | 1;
+  const int pitch = contig_pitch<TW>(mx);
   // rows per CTA (one solving thread per row, 128 threads load and store): up
   // to 32, a whole warp of recurrences, within MGR_X_SOLVE_KB of shared memory
   int R = int(std::min<size_t>(32, (size_t(MGR_X_SOLVE_KB) * 1024) / (sizeof(TW) * pitch)));
   R = std::max(1, R);
-  const size_t sm = sizeof(TW) * (size_t(R) * pitch + 2 * size_t(mx));
+  const size_t sm = solve_contig_smem<TW>(mx, R);
   const int blocks = int((lines + R - 1) / R);
   raise_smem_limit(k_solve_contig<TW>, sm);
   k_solve_contig<TW><<<blocks, 128, sm, st>>>(f, w, mx, lines, mx, R, ta, tb, op);

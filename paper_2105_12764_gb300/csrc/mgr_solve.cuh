@@ -74,15 +74,21 @@ __device__ __forceinline__ void solve_strided_line(TW* __restrict__ f, TW* __res
   }
 }
 
+#ifndef MGR_SOLVE_U32
+#define MGR_SOLVE_U32 16
+#endif
+#ifndef MGR_SOLVE_U64
+#define MGR_SOLVE_U64 8
+#endif
 template <typename TW>
 __global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* __restrict__ w, int mline,
                                                        int64_t lstride, int inner, int64_t outer, int64_t ostride,
                                                        const TW* __restrict__ ta, const TW* __restrict__ tb, int op) {
   const int64_t id = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (id >= int64_t(inner) * outer) return;
-  // 64 bytes of loads in flight per thread and sweep: sixteen FP32 or eight FP64 elements
-  // (sixteen FP64 elements cost occupancy and were slower)
-  solve_strided_line<TW, sizeof(TW) == 4 ? 16 : 8>(f, w, mline, lstride, inner, ostride, ta, tb, op, id,
+  // loads in flight per thread and sweep (build-time knobs; sixteen FP64
+  // elements cost occupancy and were slower than eight)
+  solve_strided_line<TW, sizeof(TW) == 4 ? MGR_SOLVE_U32 : MGR_SOLVE_U64>(f, w, mline, lstride, inner, ostride, ta, tb, op, id,
                                                    max(int64_t(mline) * lstride, outer * ostride));
 }
 
@@ -214,23 +220,44 @@ __global__ void __launch_bounds__(128) k_solve_staged(TW* __restrict__ f, TW* __
 // Lines along the contiguous axis: R rows of length mline (row pitch
 // row_pitch) starting at row r0 are staged in shared memory with coalesced
 // asynchronous copies by all threads; thread r < R then runs its row's
-// recurrences in register chunks of 8 (eight independent loads, eight
-// dependent FMAs, eight stores), and all threads write the rows back.  The
-// recurrence coefficients are staged once.
+// recurrences through 16-byte vectors of the staged row (one shared load,
+// E = 16 / sizeof(TW) dependent FMAs and one shared store per vector), and
+// all threads write the rows back.  The recurrence coefficients are staged
+// once, zero-padded to the pitch.
+//
+// Shared row pitch: a whole, odd number of 16-byte vectors.  A 16-byte shared
+// access is served eight threads at a time, and rows whose starts differ by
+// an odd number of vectors put those eight in different bank groups.
 template <typename TW>
-__device__ __forceinline__ size_t solve_contig_smem(int mline, int R) {
-  return sizeof(TW) * (size_t(R) * (mline | 1) + 2 * size_t(mline));
+constexpr int contig_pitch(int mline) {
+  constexpr int E = 16 / int(sizeof(TW));
+  const int v = (mline + E - 1) / E;
+  return ((v & 1) ? v : v + 1) * E;
 }
+template <typename TW>
+constexpr size_t solve_contig_smem(int mline, int R) {
+  return sizeof(TW) * (size_t(R) + 2) * size_t(contig_pitch<TW>(mline));
+}
+template <typename TW>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
 
 template <typename TW>
 __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __restrict__ w, int mline, int64_t rows,
                                                   int64_t row_pitch, int R, const TW* __restrict__ ta,
                                                   const TW* __restrict__ tb, int op, int64_t r0,
                                                   unsigned char* smem_raw) {
-  const int pitch = mline | 1;  // odd pitch spreads the rows of a warp over the banks
+  const int pitch = contig_pitch<TW>(mline);
   TW* s = reinterpret_cast<TW*>(smem_raw);  // [R][pitch]
-  TW* sa = s + R * pitch;                   // [mline]
-  TW* sb = sa + mline;                      // [mline]
+  TW* sa = s + R * pitch;                   // [pitch], zero past mline
+  TW* sb = sa + pitch;                      // [pitch], zero past mline
   const int nr = int(rows - r0 < int64_t(R) ? rows - r0 : int64_t(R));
   // rows r0 .. r0+nr-1 of mline elements at pitch row_pitch
   if (!MGR_IN((r0 + nr - 1) * row_pitch + mline - 1, rows * row_pitch, kDbgSolveF)) return;
@@ -244,42 +271,64 @@ __device__ __forceinline__ void solve_contig_rows(TW* __restrict__ f, TW* __rest
     for (int c = lane; c < mline; c += 32) cp_async(dst + c, src + c, int(sizeof(TW)));
   }
   cp_commit();
-  for (int q = threadIdx.x; q < mline; q += blockDim.x) {
-    sa[q] = ta[q];
-    sb[q] = tb[q];
+  for (int q = threadIdx.x; q < pitch; q += blockDim.x) {
+    sa[q] = q < mline ? ta[q] : TW(0);
+    sb[q] = q < mline ? tb[q] : TW(0);
   }
   cp_wait<0>();
   __syncthreads();
   if (threadIdx.x < nr) {
-    TW* l = s + threadIdx.x * pitch;
-    constexpr int U = 8;
+    using V = typename Vec16<TW>::type;
+    constexpr int E = 16 / int(sizeof(TW));
+    V* l = reinterpret_cast<V*>(s + threadIdx.x * pitch);
+    const V* av = reinterpret_cast<const V*>(sa);
+    const V* bv = reinterpret_cast<const V*>(sb);
+    const int nv = (mline + E - 1) / E;  // vectors holding the row's elements
+    // forward: the elements past mline in the last vector follow every real
+    // one, so computing on them (the padding) changes nothing that is kept
     TW prev = TW(0);
-    for (int q0 = 0; q0 < mline; q0 += U) {
-      TW v[U];
+#pragma unroll 2
+    for (int i = 0; i < nv; ++i) {
+      alignas(16) TW x[E];
+      alignas(16) TW a[E];
+      *reinterpret_cast<V*>(x) = l[i];
+      *reinterpret_cast<V*>(a) = av[i];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = (q0 + u < mline) ? l[q0 + u] : TW(0);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        prev = v[u] - sa[min(q0 + u, mline - 1)] * prev;
-        v[u] = prev;
+      for (int e = 0; e < E; ++e) {
+        prev = x[e] - a[e] * prev;
+        x[e] = prev;
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q0 + u < mline) l[q0 + u] = v[u];
+      l[i] = *reinterpret_cast<const V*>(x);
     }
+    // backward from element mline-1: in the last vector the elements past
+    // mline are skipped
     TW next = TW(0);
-    for (int q1 = mline - 1; q1 >= 0; q1 -= U) {
-      TW v[U];
+    {
+      const int i = nv - 1;
+      alignas(16) TW x[E];
+      alignas(16) TW b[E];
+      *reinterpret_cast<V*>(x) = l[i];
+      *reinterpret_cast<V*>(b) = bv[i];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = (q1 - u >= 0) ? l[q1 - u] : TW(0);
+      for (int e = E - 1; e >= 0; --e)
+        if (i * E + e < mline) {
+          next = x[e] - b[e] * next;
+          x[e] = next;
+        }
+      l[i] = *reinterpret_cast<const V*>(x);
+    }
+#pragma unroll 2
+    for (int i = nv - 2; i >= 0; --i) {
+      alignas(16) TW x[E];
+      alignas(16) TW b[E];
+      *reinterpret_cast<V*>(x) = l[i];
+      *reinterpret_cast<V*>(b) = bv[i];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        next = v[u] - sb[max(q1 - u, 0)] * next;
-        v[u] = next;
+      for (int e = E - 1; e >= 0; --e) {
+        next = x[e] - b[e] * next;
+        x[e] = next;
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (q1 - u >= 0) l[q1 - u] = v[u];
+      l[i] = *reinterpret_cast<const V*>(x);
     }
   }
   __syncthreads();
