@@ -261,6 +261,14 @@ cudaError_t solve_axis(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op,
   return err;
 }
 
+// Strided axes: whole lines staged in shared memory below this many lines
+// (build-time knobs), one thread per line from global memory above.
+#ifndef MGR_STAGED_LINES_F32
+#define MGR_STAGED_LINES_F32 32768
+#endif
+#ifndef MGR_STAGED_LINES_F64
+#define MGR_STAGED_LINES_F64 32768
+#endif
 template <typename TW>
 cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, int op, cudaStream_t st) {
   const LevelGeom& g = p->geom[l];
@@ -279,7 +287,8 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   }
   const int64_t lines = int64_t(inner) * outer;
   const size_t ssm = solve_staged_smem<TW>(mline);
-  if (lines < 32768 && ssm <= size_t(100) * 1024 && ssm <= p->ctx->smem_optin) {
+  const int64_t staged_below = sizeof(TW) == 4 ? int64_t(MGR_STAGED_LINES_F32) : int64_t(MGR_STAGED_LINES_F64);
+  if (lines < staged_below && ssm <= size_t(100) * 1024 && ssm <= p->ctx->smem_optin) {
     // few lines (coarse levels): whole lines staged in shared memory, 32 per CTA
     raise_smem_limit(k_solve_staged<TW>, ssm);
     k_solve_staged<TW><<<int((lines + kStagedLines - 1) / kStagedLines), 128, ssm, st>>>(f, w, mline, lstride, inner,
