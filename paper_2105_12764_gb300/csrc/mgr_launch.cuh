@@ -297,13 +297,6 @@ cudaError_t solve_axis_launch(const mgr_plan* p, int l, int axis, TW* f, TW* w, 
   }
   const int threads = 128;
   const int blocks = int((lines + threads - 1) / threads);
-  if (MGR_SOLVE_ASYNC) {
-    constexpr size_t sm = solve_async_smem<TW, async_chunk<TW>(), kAsyncNB>(kAsyncThreads);
-    raise_smem_limit(k_solve_strided_async<TW>, sm);
-    k_solve_strided_async<TW><<<blocks, kAsyncThreads, sm, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb,
-                                                                 op);
-    return cudaGetLastError();
-  }
   k_solve_strided<TW><<<blocks, threads, 0, st>>>(f, w, mline, lstride, inner, outer, ostride, ta, tb, op);
   return cudaGetLastError();
 }

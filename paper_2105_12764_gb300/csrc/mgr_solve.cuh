@@ -92,123 +92,6 @@ __global__ void __launch_bounds__(128) k_solve_strided(TW* __restrict__ f, TW* _
                                                    max(int64_t(mline) * lstride, outer * ostride));
 }
 
-// Lines along a strided axis, one thread per line as above, with the line's
-// elements brought into this thread's own shared-memory slots by asynchronous
-// copies: NB buffers of C elements, NB-1 of them in flight while the
-// recurrence runs through the oldest (no registers hold the loads in flight,
-// so more of them can be).  The backward sweep prefetches the forward sweep's
-// results (and, for the correction, the coarse values) the same way.  Slot
-// (b, u) of thread t is element (b*C + u)*blockDim.x + t of `sbuf` (two such
-// arrays: the line's values and the correction operand).
-template <typename TW, int C, int NB>
-constexpr size_t solve_async_smem(int threads) {
-  return sizeof(TW) * 2 * size_t(NB) * C * size_t(threads);
-}
-
-template <typename TW, int C, int NB>
-__device__ __forceinline__ void solve_strided_line_async(TW* __restrict__ f, TW* __restrict__ w, int mline,
-                                                         int64_t lstride, int inner, int64_t ostride,
-                                                         const TW* __restrict__ ta, const TW* __restrict__ tb, int op,
-                                                         int64_t line, long long ext, TW* sbuf) {
-  (void)ext;
-  const int i = int(line % inner);
-  const int64_t o = line / inner;
-  if (!MGR_IN(o * ostride + i, ext, kDbgSolveF) || !MGR_IN(o * ostride + i + int64_t(mline - 1) * lstride, ext, kDbgSolveF))
-    return;
-  const int nt = blockDim.x, tid = threadIdx.x;
-  TW* fl = f + o * ostride + i;
-  TW* wl = w + o * ostride + i;
-  TW* sv = sbuf;                    // [NB][C][nt] the line's values
-  TW* sw = sbuf + NB * C * nt;      // [NB][C][nt] the correction operand
-  const int nch = (mline + C - 1) / C;
-  // forward sweep, chunk k = elements k*C .. k*C+C-1
-  auto issue_fwd = [&](int k) {
-    if (k < nch) {
-      TW* b = sv + (k % NB) * C * nt + tid;
-#pragma unroll
-      for (int u = 0; u < C; ++u)
-        if (k * C + u < mline) cp_async(b + u * nt, fl + int64_t(k * C + u) * lstride, int(sizeof(TW)));
-    }
-    cp_commit();  // (an empty group past the end keeps the group count uniform)
-  };
-#pragma unroll
-  for (int k = 0; k < NB - 1; ++k) issue_fwd(k);
-  TW prev = TW(0);
-  for (int k = 0; k < nch; ++k) {
-    issue_fwd(k + NB - 1);  // into the buffer chunk k-1 used
-    cp_wait<NB - 1>();      // chunk k has arrived
-    const TW* b = sv + (k % NB) * C * nt + tid;
-#pragma unroll
-    for (int u = 0; u < C; ++u) {
-      const int q = k * C + u;
-      if (q < mline) {
-        prev = b[u * nt] - ta[q] * prev;
-        fl[int64_t(q) * lstride] = prev;
-      }
-    }
-  }
-  cp_wait<0>();
-  __threadfence_block();  // this thread's forward results before it copies them back in
-  // backward sweep, chunk k = elements mline-1-k*C .. mline-C-k*C (descending)
-  auto issue_bwd = [&](int k) {
-    if (k < nch) {
-      TW* b = sv + (k % NB) * C * nt + tid;
-      TW* bw = sw + (k % NB) * C * nt + tid;
-#pragma unroll
-      for (int u = 0; u < C; ++u) {
-        const int q = mline - 1 - k * C - u;
-        if (q >= 0) {
-          cp_async(b + u * nt, fl + int64_t(q) * lstride, int(sizeof(TW)));
-          if (op != SOLVE_INPLACE) cp_async(bw + u * nt, wl + int64_t(q) * lstride, int(sizeof(TW)));
-        }
-      }
-    }
-    cp_commit();
-  };
-#pragma unroll
-  for (int k = 0; k < NB - 1; ++k) issue_bwd(k);
-  TW next = TW(0);
-  for (int k = 0; k < nch; ++k) {
-    issue_bwd(k + NB - 1);
-    cp_wait<NB - 1>();
-    const TW* b = sv + (k % NB) * C * nt + tid;
-    const TW* bw = sw + (k % NB) * C * nt + tid;
-#pragma unroll
-    for (int u = 0; u < C; ++u) {
-      const int q = mline - 1 - k * C - u;
-      if (q >= 0) {
-        next = b[u * nt] - tb[q] * next;
-        if (op == SOLVE_INPLACE) fl[int64_t(q) * lstride] = next;
-        else if (op == SOLVE_ADD) wl[int64_t(q) * lstride] = bw[u * nt] + next;
-        else wl[int64_t(q) * lstride] = bw[u * nt] - next;
-      }
-    }
-  }
-  cp_wait<0>();
-}
-
-#ifndef MGR_SOLVE_ASYNC
-#define MGR_SOLVE_ASYNC 0
-#endif
-constexpr int kAsyncThreads = 128, kAsyncNB = 4;
-template <typename TW>
-constexpr int async_chunk() {
-  return sizeof(TW) == 4 ? 8 : 4;
-}
-template <typename TW>
-__global__ void __launch_bounds__(kAsyncThreads) k_solve_strided_async(TW* __restrict__ f, TW* __restrict__ w,
-                                                                       int mline, int64_t lstride, int inner,
-                                                                       int64_t outer, int64_t ostride,
-                                                                       const TW* __restrict__ ta,
-                                                                       const TW* __restrict__ tb, int op) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t id = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (id >= int64_t(inner) * outer) return;
-  solve_strided_line_async<TW, async_chunk<TW>(), kAsyncNB>(f, w, mline, lstride, inner, ostride, ta, tb, op, id,
-                                                            max(int64_t(mline) * lstride, outer * ostride),
-                                                            reinterpret_cast<TW*>(smem_raw));
-}
-
 // Lines along a strided axis, 32 per CTA, staged whole in shared memory: the
 // CTA's lines (consecutive line indices, so each step q is one or two
 // contiguous row segments) are copied in with asynchronous copies all in
