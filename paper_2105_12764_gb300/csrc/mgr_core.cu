@@ -468,7 +468,7 @@ cudaError_t host_pipe_t(const mgr_plan* p, const void* host_in, void* host_out, 
   const int nz = int(p->full[0]), mz = p->geom[L].ax[0].m;
   const size_t plane = size_t(p->full[1]) * size_t(p->full[2]) * sizeof(TD);
   auto a = level_args<TS, TW>(p, L);
-  const dim3 grid = level_grid(p, a);
+  const dim3 grid = level_grid<0>(p, a);
   const int gz = int(grid.z), qc = a.qz_chunk;
   const int parts = std::min(gz, kPipeParts);
   int c0[kPipeParts + 1];
@@ -535,7 +535,7 @@ cudaError_t host_rec_pipe_t(const mgr_plan* p, const void* host_in, void* host_o
   const int nz = int(p->full[0]), mz = p->geom[L].ax[0].m;
   const size_t plane = size_t(p->full[1]) * size_t(p->full[2]) * sizeof(TD);
   auto a = level_args<TS, TW>(p, L);
-  const int gz = int(level_grid(p, a).z), qc = a.qz_chunk;
+  const int gz = int(level_grid<1>(p, a).z), qc = a.qz_chunk;
   const int parts = std::min(gz, kPipeParts);
   int c0[kPipeParts + 1];
   for (int k = 0; k <= parts; ++k) c0[k] = int((int64_t(k) * gz) / parts);

@@ -100,9 +100,9 @@ inline int choose_chunks(const mgr_plan* p, int64_t tiles, int mz, int ctas_per_
   return best;
 }
 
-template <typename TS, typename TW>
+template <int MODE, typename TS, typename TW>
 dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
-  using C = LevelCfg<TS>;
+  using C = LevelCfgM<TS, MODE>;
   using G = LevelTile<C::NW, C::RPW>;
   const int gx = (a.m[2] + G::BX - 1) / G::BX, gy = (a.m[1] + G::BY - 1) / G::BY;
   const int chunks = choose_chunks(p, int64_t(gx) * gy, a.m[0], level_ctas_per_sm(C::NW), kLevelMaxChunk);
@@ -113,11 +113,11 @@ dim3 level_grid(const mgr_plan* p, LevelArgs<TS, TW>& a) {
 
 template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
-  using C = LevelCfg<TS>;
+  using C = LevelCfgM<TS, MODE>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
   raise_smem_limit(kern, sm);
-  dim3 grid = level_grid(p, a);
+  dim3 grid = level_grid<MODE>(p, a);
   kern<<<grid, C::NW * 32, sm, st>>>(a);
 }
 
@@ -126,11 +126,11 @@ void launch_level(const mgr_plan* p, LevelArgs<TS, TW>& a, cudaStream_t st) {
 // planes are ready.
 template <int MODE, typename TI, typename TD, typename TS, typename TW, bool PK, bool QZ = false>
 void launch_level_chunks(const mgr_plan* p, LevelArgs<TS, TW>& a, int c0, int c1, cudaStream_t st) {
-  using C = LevelCfg<TS>;
+  using C = LevelCfgM<TS, MODE>;
   constexpr size_t sm = level_smem_bytes<C::NW, C::RPW, C::STAGES, TI, TS>();
   auto kern = k_level<MODE, C::NW, C::RPW, C::STAGES, TI, TD, TS, TW, PK, QZ>;
   raise_smem_limit(kern, sm);
-  dim3 grid = level_grid(p, a);
+  dim3 grid = level_grid<MODE>(p, a);
   if (c1 <= c0 || c1 > int(grid.z)) return;
   a.bz0 = c0;
   grid.z = unsigned(c1 - c0);

@@ -100,6 +100,20 @@ struct LevelCfg<float> {
   static constexpr int NW = MGR_LEVEL_F32_NW, RPW = MGR_LEVEL_F32_RPW, STAGES = MGR_LEVEL_F32_STAGES;
 };
 
+// Tile configuration per pass: the recomposition load pass (MODE 1) computes
+// no coefficients and keeps fewer values per row pair in registers, so in FP32
+// it also fits three row pairs per warp (a taller tile, less repeated halo
+// work) within the same 128 registers; MGR_LEVEL_F32_REC_RPW selects it at
+// build time (measured: faster at 1000x700x300, slower at 513^3; default two).
+#ifndef MGR_LEVEL_F32_REC_RPW
+#define MGR_LEVEL_F32_REC_RPW 2
+#endif
+template <typename TS, int MODE>
+struct LevelCfgM {
+  static constexpr int NW = LevelCfg<TS>::NW, STAGES = LevelCfg<TS>::STAGES;
+  static constexpr int RPW = (MODE == 1 && sizeof(TS) == 4) ? MGR_LEVEL_F32_REC_RPW : LevelCfg<TS>::RPW;
+};
+
 // CTAs per SM a level-pass or interpolation CTA of NW warps is compiled for:
 // 16 warps per SM in every configuration, so each thread may use up to 128
 // registers.
