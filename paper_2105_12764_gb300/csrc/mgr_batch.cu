@@ -21,9 +21,9 @@
 // field's items).  The model charges each work item the shared-memory slots
 // it streams (halo and padding included) and takes the longer of the memory
 // time and the longest-processing-time schedule of the items over the
-// persistent CTAs; the model's best candidate of each tile shape, and the
-// next best up to three, are timed on the real batch and the fastest is
-// cached per batch shape.
+// persistent CTAs; the model's best candidate of each tile shape, the next
+// best up to three, and the other chunk lengths of the fastest tile shape are
+// timed on the real batch and the fastest is cached per batch shape.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -975,8 +975,8 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
     }
   std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
   // measured: the model's best candidate of every tile shape, then the next
-  // best overall up to three (the model ranks chunk lengths well, tile
-  // shapes less so)
+  // best overall up to three, then every other chunk length of the fastest
+  // tile shape
   std::vector<TileCand> timed;
   for (int cfg = 0; cfg < kNumCfg; ++cfg)
     for (const auto& r : ranked)
@@ -993,7 +993,7 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
   TileCand best = ranked[0].second;
   double best_ms = 1e30;
   std::vector<std::pair<TileCand, double>> log;
-  for (const TileCand& c : timed) {
+  auto time_one = [&](const TileCand& c) {
     std::string why;
     const double ms = time_candidate<TD, TS, TW>(ctx, fields, op, c, B.stream, &why);
     log.push_back({c, ms});
@@ -1001,6 +1001,16 @@ TileCand autotune(mgr_ctx* ctx, BatchState& B, const std::vector<FieldRef>& fiel
     if (ms >= 0.0 && ms < best_ms) {
       best_ms = ms;
       best = c;
+    }
+  };
+  for (const TileCand& c : timed) time_one(c);
+  // then the other chunk lengths of the fastest tile shape
+  if (best_ms < 1e30) {
+    const int cfg = best.cfg;
+    for (int chunk : kChunks) {
+      bool seen = false;
+      for (const TileCand& c : timed) seen |= c.cfg == cfg && c.chunk == chunk;
+      if (!seen) time_one(TileCand{cfg, chunk});
     }
   }
   B.tuned[skey] = best;
